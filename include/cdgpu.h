@@ -1,0 +1,168 @@
+/*
+ * cdgpu — community detection (Label Propagation and Louvain) on one GPU.
+ *
+ * C ABI of libcdgpu.so. Every call takes plain pointers and sizes; a flag
+ * says whether a caller buffer lives in host or device memory. All device
+ * work of a graph runs on the CUDA stream given at upload, in the order the
+ * calls are made; every call returns after its results are valid in the
+ * caller's buffers.
+ *
+ * Method (arXiv 2507.06471, "Designing Parallel Algorithms for Community
+ * Detection using Arachne"):
+ *   - graph model, weighted degree, volume, cut: Sec. II-A
+ *   - modularity and the move gain (Eq. deltaQ): Sec. II-C
+ *   - Label Propagation: Algorithm 1 (PLP / PLPMove), Sec. III-A
+ *   - Louvain local moving: Algorithm 2, Sec. III-B-1
+ *   - Louvain aggregation and driver: Algorithm 3, Sec. III-B-2
+ *
+ * Schedule (fixed so that results are reproducible bit for bit; the paper's
+ * Chapel loops are asynchronous): rounds are synchronous — every decision
+ * reads the labels and community volumes of the start of the round, then all
+ * moves apply at once. A vertex whose decision differs from its label commits
+ * the move in round r of level l only if bit 63 of SplitMix64 draw number
+ * (l << 48 | r << 32 | v) from state `sched_seed` is set, else it defers to
+ * the next round (it stays active). Louvain moves need a strictly positive
+ * gain, ties go to the smallest community id, and a singleton joins another
+ * singleton only if that one has the smaller id. LPA keeps the current label
+ * when it attains the maximum weight, else takes the smallest maximal label.
+ * The next round examines the moved vertices, their neighbours and the
+ * deferred vertices.
+ *
+ * Graph input convention: a symmetric CSR. A non-loop edge {u,v} of weight w
+ * is the two arcs u->v and v->u, each carrying w; a loop of weight L on v is
+ * the single arc v->v carrying L (deg_w counts it twice, Sec. II-A). Vertex
+ * ids are int32 in [0, n); weights are int32 >= 1, or NULL for unit weights.
+ */
+#ifndef CDGPU_H
+#define CDGPU_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes: 0 on success, a negative code otherwise. */
+#define CD_OK 0
+#define CD_EINVAL (-1)    /* null pointer, bad size, weight < 1, bad label   */
+#define CD_EBOUNDS (-2)   /* a column id outside [0, n)                      */
+#define CD_ENOMEM (-3)    /* device allocation failed                        */
+#define CD_ECUDA (-4)     /* a CUDA runtime error (see cd_last_cuda_error)   */
+#define CD_EOVERFLOW (-5) /* vol(V) >= 2^62 or n >= 2^31                     */
+#define CD_ETIMEOUT (-6)  /* a bounded device wait ran out                   */
+#define CD_ENOTSYM (-7)   /* offsets not monotone / arcs not paired          */
+
+typedef struct cd_graph cd_graph; /* opaque; owns a device copy of the CSR */
+
+typedef struct cd_params {
+  int32_t max_iter;         /* rounds at most: per call (LPA) or per level (Louvain); default 100 */
+  int32_t max_levels;       /* Louvain levels at most; default 64 */
+  int64_t threshold;        /* LPA stops after a round with moved + deferred <= threshold; default 0 */
+  int32_t tie_keep_current; /* LPA tie rule: 1 keep the current label on a tie (default), 0 smallest */
+  int32_t singleton_rule;   /* Louvain: 1 (default) singleton joins only a smaller-id singleton */
+  int32_t use_frontier;     /* 1 (default): examine only flagged vertices; 0: all, every round */
+  int32_t timing;           /* 1: record CUDA-event times per round and per kernel (trace/profile) */
+  uint64_t sched_seed;      /* state of the deferral coin's SplitMix64 stream; default 0x5EED5EED */
+} cd_params;
+
+/* Per-round record of the last run on a graph (cd_trace_get). */
+typedef struct cd_round_trace {
+  int32_t level;    /* Louvain level (0 for LPA) */
+  int32_t round;    /* round within the level */
+  int64_t active;   /* vertices examined */
+  int64_t arcs;     /* arcs scanned = sum of row lengths of examined vertices */
+  int64_t moved;    /* vertices that changed label */
+  int64_t deferred; /* vertices whose move was deferred by the coin */
+  float scan_ms;    /* device time of the scan kernels (timing = 1) */
+  float round_ms;   /* device time of the whole round (timing = 1) */
+} cd_round_trace;
+
+/* Per-kernel totals of the last run (cd_profile_get; timing = 1). */
+typedef struct cd_kernel_profile {
+  char name[32];
+  int64_t launches;
+  double total_ms;  /* sum of CUDA-event durations of its launches */
+  double alg_bytes; /* algorithmic bytes moved by all its launches */
+} cd_kernel_profile;
+
+/* Fill *p with the defaults listed above. */
+int cd_params_default(cd_params* p);
+
+/* Sec. II-A: copy a symmetric CSR into library-owned device memory,
+ * validate it (columns in range, offsets monotone, weights >= 1) and compute
+ * deg_w(v) (loops counted twice) and vol(V). offsets has n+1 entries (int64
+ * if offsets_is_i64, else int32) with offsets[0] = 0 and offsets[n] = nnz;
+ * cols has nnz int32 entries; w has nnz int32 entries or is NULL (unit
+ * weights). ptrs_on_device says whether the three arrays are device (1) or
+ * host (0) pointers; the caller keeps ownership of them. stream is a
+ * cudaStream_t (NULL = the legacy default stream). *out receives the handle.
+ * Errors: CD_EINVAL, CD_EBOUNDS, CD_ENOTSYM, CD_EOVERFLOW, CD_ENOMEM, CD_ECUDA. */
+int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols,
+                  const int32_t* w, int64_t n, int64_t nnz, int ptrs_on_device,
+                  void* stream, cd_graph** out);
+
+/* Release a handle and all device memory it owns. NULL is accepted. */
+int cd_graph_free(cd_graph* g);
+
+/* Sizes of a handle: vertices, arcs, vol(V). Any output may be NULL. */
+int cd_graph_info(const cd_graph* g, int64_t* n, int64_t* nnz, int64_t* vol);
+
+/* Copy the CSR of a handle out in the input convention (a loop arc carries
+ * L). off: n+1 int64, cols: nnz int32, w: nnz int64 (may be NULL).
+ * Coarse graphs from cd_louvain_aggregate have rows grouped by vertex but
+ * columns in no particular order. */
+int cd_graph_download(const cd_graph* g, int64_t* off, int32_t* cols, int64_t* w,
+                      int ptrs_on_device);
+
+/* Algorithm 1 (PLP): labels start as vertex ids; rounds run until
+ * moved + deferred <= threshold or max_iter rounds. labels_out: n int32
+ * (host or device per on_device). *rounds_out (may be NULL) = rounds run. */
+int cd_lpa_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
+               int32_t* rounds_out);
+
+/* Algorithm 2 (local moving) on g. If init_given is 0 the partition starts as
+ * singletons (comID = vertex id), else from labels_io (n int32 in [0, n)).
+ * Runs until a round in which no vertex moves or defers, or max_iter rounds;
+ * uses coin level 0. labels_io receives comID. *moves_out (may be NULL) =
+ * total moves; *rounds_out (may be NULL) = rounds run. */
+int cd_louvain_local_move(cd_graph* g, const cd_params* p, int32_t* labels_io, int init_given,
+                          int on_device, int64_t* moves_out, int32_t* rounds_out);
+
+/* Algorithm 3, Aggregation: remap the communities of `labels` (n int32 in
+ * [0, n)) to 0..k-1 in ascending id order and build the coarse graph in which
+ * edge {A,B} carries the summed weight of the edges between A and B (a loop
+ * {A,A} carries A's internal weight). *coarse_out receives a new handle on
+ * the same stream; newid_out (n int32, may be NULL) receives the new id of
+ * every community id (-1 if unused); *k_out = k. */
+int cd_louvain_aggregate(cd_graph* g, const int32_t* labels, int on_device, cd_graph** coarse_out,
+                         int32_t* newid_out, int64_t* k_out);
+
+/* Sec. II-C: modularity of `labels` (n int32 in [0, n)) on g, exact in
+ * integers: Q = (I vol - sum_c vol(c)^2) / vol^2 with I = sum of the arc
+ * weights inside communities (loops twice); the quotient is taken in FP64.
+ * Q = 0 when vol(V) = 0. */
+int cd_modularity(cd_graph* g, const int32_t* labels, int on_device, double* q_out);
+
+/* Algorithm 3 (Louvain): local moving (coin level = level index) and
+ * aggregation until a level ends with every vertex in its own community, or
+ * max_levels levels. labels_out: n int32, the final community of every input
+ * vertex, contiguous ids. *levels_out and *q_out (modularity on g) may be
+ * NULL. */
+int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
+                   int32_t* levels_out, double* q_out);
+
+/* Copy up to cap per-round records of the last run on g into out; *count
+ * receives the number of records available. */
+int cd_trace_get(const cd_graph* g, cd_round_trace* out, int32_t cap, int32_t* count);
+
+/* Copy up to cap per-kernel profiles of the last run on g (timing = 1). */
+int cd_profile_get(const cd_graph* g, cd_kernel_profile* out, int32_t cap, int32_t* count);
+
+/* Human-readable text of a status code. */
+const char* cd_status_string(int status);
+
+/* The last CUDA runtime error seen by the library (cudaError_t as int). */
+int cd_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,290 @@
+"""Python binding of libcdgpu (community detection on one GB300 GPU).
+
+Argument marshalling only: every function below forwards to the C entry point
+of the same name in ``libcdgpu.so`` (declared in ``include/cdgpu.h``); all
+compute runs in the library's CUDA kernels. PyTorch is used for device memory
+and streams. There is no CPU fallback: if the library cannot be loaded the
+calls raise.
+
+Method: arXiv 2507.06471 — Label Propagation (Algorithm 1), Louvain local
+moving (Algorithm 2, Eq. deltaQ) and aggregation (Algorithm 3), modularity
+(Sec. II-C), under the synchronous schedule described in ``cdgpu.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import _build
+
+CD_OK, CD_EINVAL, CD_EBOUNDS, CD_ENOMEM, CD_ECUDA, CD_EOVERFLOW, CD_ETIMEOUT, CD_ENOTSYM = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+
+EXPORTED = [
+    "cd_params_default", "cd_csr_upload", "cd_graph_free", "cd_graph_info", "cd_graph_download",
+    "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
+    "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
+]
+
+
+class cd_params(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("max_levels", ctypes.c_int32),
+                ("threshold", ctypes.c_int64), ("tie_keep_current", ctypes.c_int32),
+                ("singleton_rule", ctypes.c_int32), ("use_frontier", ctypes.c_int32),
+                ("timing", ctypes.c_int32), ("sched_seed", ctypes.c_uint64)]
+
+
+class cd_round_trace(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("round", ctypes.c_int32), ("active", ctypes.c_int64),
+                ("arcs", ctypes.c_int64), ("moved", ctypes.c_int64), ("deferred", ctypes.c_int64),
+                ("scan_ms", ctypes.c_float), ("round_ms", ctypes.c_float)]
+
+
+class cd_kernel_profile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double), ("alg_bytes", ctypes.c_double)]
+
+
+class CDError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.cd_status_string(status).decode() if _lib else str(status)
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """Load libcdgpu.so (building it first if the sources changed)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.cd_params_default.argtypes = [ctypes.POINTER(cd_params)]
+        L.cd_csr_upload.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int, _P, ctypes.POINTER(_P)]
+        L.cd_graph_free.argtypes = [_P]
+        L.cd_graph_info.argtypes = [_P, _P, _P, _P]
+        L.cd_graph_download.argtypes = [_P, _P, _P, _P, ctypes.c_int]
+        L.cd_lpa_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P]
+        L.cd_louvain_local_move.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int,
+                                            ctypes.c_int, _P, _P]
+        L.cd_louvain_aggregate.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(_P), _P, _P]
+        L.cd_modularity.argtypes = [_P, _P, ctypes.c_int, _P]
+        L.cd_louvain_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P, _P]
+        L.cd_trace_get.argtypes = [_P, _P, ctypes.c_int32, _P]
+        L.cd_profile_get.argtypes = [_P, _P, ctypes.c_int32, _P]
+        L.cd_status_string.restype = ctypes.c_char_p
+        L.cd_status_string.argtypes = [ctypes.c_int]
+        L.cd_last_cuda_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != CD_OK:
+        raise CDError(rc, where)
+
+
+def _ptr(x):
+    """(pointer, on_device) of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None, 0
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda)
+    return x.ctypes.data_as(ctypes.c_void_p), 0
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------------------------ same-name entry points
+
+def cd_params_default(**overrides) -> cd_params:
+    p = cd_params()
+    _check(lib().cd_params_default(ctypes.byref(p)), "cd_params_default")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def cd_csr_upload(offsets, cols, w=None, n: Optional[int] = None, stream=None) -> ctypes.c_void_p:
+    """Upload a symmetric CSR (torch tensors on one device, or numpy arrays)."""
+    n = (len(offsets) - 1) if n is None else n
+    nnz = int(len(cols))
+    po, dev_o = _ptr(offsets)
+    pc, dev_c = _ptr(cols)
+    pw, dev_w = _ptr(w)
+    if w is not None and dev_w != dev_o:
+        raise ValueError("offsets, cols and w must live on the same side (host or device)")
+    if dev_o != dev_c:
+        raise ValueError("offsets and cols must live on the same side (host or device)")
+    is64 = int(str(offsets.dtype).endswith("int64"))
+    if not is64 and not str(offsets.dtype).endswith("int32"):
+        raise TypeError("offsets must be int32 or int64")
+    if not str(cols.dtype).endswith("int32") or (w is not None and not str(w.dtype).endswith("int32")):
+        raise TypeError("cols and w must be int32")
+    out = ctypes.c_void_p()
+    _check(lib().cd_csr_upload(po, is64, pc, pw, n, nnz, dev_o, _stream_ptr(stream), ctypes.byref(out)),
+           "cd_csr_upload")
+    return out
+
+
+def cd_graph_free(g) -> None:
+    _check(lib().cd_graph_free(g), "cd_graph_free")
+
+
+def cd_graph_info(g):
+    n, nnz, vol = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().cd_graph_info(g, ctypes.byref(n), ctypes.byref(nnz), ctypes.byref(vol)), "cd_graph_info")
+    return n.value, nnz.value, vol.value
+
+
+def cd_graph_download(g):
+    """(off int64[n+1], cols int32[nnz], w int64[nnz]) host arrays, loops as L."""
+    n, nnz, _ = cd_graph_info(g)
+    off = np.zeros(n + 1, dtype=np.int64)
+    cols = np.zeros(max(nnz, 1), dtype=np.int32)
+    w = np.zeros(max(nnz, 1), dtype=np.int64)
+    _check(lib().cd_graph_download(g, _ptr(off)[0], _ptr(cols)[0], _ptr(w)[0], 0), "cd_graph_download")
+    return off, cols[:nnz], w[:nnz]
+
+
+def cd_lpa_run(g, params: cd_params, labels_out):
+    p, dev = _ptr(labels_out)
+    r = ctypes.c_int32()
+    _check(lib().cd_lpa_run(g, ctypes.byref(params), p, dev, ctypes.byref(r)), "cd_lpa_run")
+    return r.value
+
+
+def cd_louvain_local_move(g, params: cd_params, labels_io, init_given: bool = False):
+    p, dev = _ptr(labels_io)
+    mv, r = ctypes.c_int64(), ctypes.c_int32()
+    _check(lib().cd_louvain_local_move(g, ctypes.byref(params), p, int(init_given), dev,
+                                       ctypes.byref(mv), ctypes.byref(r)), "cd_louvain_local_move")
+    return mv.value, r.value
+
+
+def cd_louvain_aggregate(g, labels, newid_out=None):
+    p, dev = _ptr(labels)
+    pn, devn = _ptr(newid_out)
+    if newid_out is not None and devn != dev:
+        raise ValueError("labels and newid_out must live on the same side")
+    out, k = ctypes.c_void_p(), ctypes.c_int64()
+    _check(lib().cd_louvain_aggregate(g, p, dev, ctypes.byref(out), pn, ctypes.byref(k)),
+           "cd_louvain_aggregate")
+    return out, k.value
+
+
+def cd_modularity(g, labels) -> float:
+    p, dev = _ptr(labels)
+    q = ctypes.c_double()
+    _check(lib().cd_modularity(g, p, dev, ctypes.byref(q)), "cd_modularity")
+    return q.value
+
+
+def cd_louvain_run(g, params: cd_params, labels_out):
+    p, dev = _ptr(labels_out)
+    lv, q = ctypes.c_int32(), ctypes.c_double()
+    _check(lib().cd_louvain_run(g, ctypes.byref(params), p, dev, ctypes.byref(lv), ctypes.byref(q)),
+           "cd_louvain_run")
+    return lv.value, q.value
+
+
+def cd_trace_get(g):
+    cnt = ctypes.c_int32()
+    _check(lib().cd_trace_get(g, None, 0, ctypes.byref(cnt)), "cd_trace_get")
+    buf = (cd_round_trace * max(cnt.value, 1))()
+    _check(lib().cd_trace_get(g, buf, cnt.value, ctypes.byref(cnt)), "cd_trace_get")
+    return [{f: getattr(buf[i], f) for f, _ in cd_round_trace._fields_} for i in range(cnt.value)]
+
+
+def cd_profile_get(g):
+    cnt = ctypes.c_int32()
+    buf = (cd_kernel_profile * 64)()
+    _check(lib().cd_profile_get(g, buf, 64, ctypes.byref(cnt)), "cd_profile_get")
+    return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "total_ms": buf[i].total_ms,
+             "alg_bytes": buf[i].alg_bytes} for i in range(min(cnt.value, 64))]
+
+
+def cd_status_string(status: int) -> str:
+    return lib().cd_status_string(status).decode()
+
+
+# ------------------------------------------------------------------ convenience handle
+
+class Graph:
+    """Owns a cd_graph handle; methods forward to the entry points above."""
+
+    def __init__(self, offsets, cols, w=None, stream=None):
+        self.h = cd_csr_upload(offsets, cols, w, stream=stream)
+        self.n, self.nnz, self.vol = cd_graph_info(self.h)
+
+    @classmethod
+    def _adopt(cls, h):
+        g = cls.__new__(cls)
+        g.h = h
+        g.n, g.nnz, g.vol = cd_graph_info(h)
+        return g
+
+    def close(self):
+        if getattr(self, "h", None):
+            cd_graph_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _labels(self, device):
+        import torch
+        return torch.empty(self.n, dtype=torch.int32, device=device)
+
+    def lpa(self, params=None, device="cuda", **kw):
+        params = params or cd_params_default(**kw)
+        lab = self._labels(device)
+        rounds = cd_lpa_run(self.h, params, lab)
+        return lab, rounds
+
+    def local_move(self, params=None, labels=None, device="cuda", **kw):
+        params = params or cd_params_default(**kw)
+        if labels is None:
+            lab = self._labels(device)
+            moves, rounds = cd_louvain_local_move(self.h, params, lab, False)
+        else:
+            lab = labels.clone()
+            moves, rounds = cd_louvain_local_move(self.h, params, lab, True)
+        return lab, moves, rounds
+
+    def louvain(self, params=None, device="cuda", **kw):
+        params = params or cd_params_default(**kw)
+        lab = self._labels(device)
+        levels, q = cd_louvain_run(self.h, params, lab)
+        return lab, levels, q
+
+    def aggregate(self, labels, newid_out=None):
+        h, k = cd_louvain_aggregate(self.h, labels, newid_out)
+        return Graph._adopt(h), k
+
+    def modularity(self, labels) -> float:
+        return cd_modularity(self.h, labels)
+
+    def download(self):
+        return cd_graph_download(self.h)
+
+    def trace(self):
+        return cd_trace_get(self.h)
+
+    def profile(self):
+        return cd_profile_get(self.h)

@@ -1,0 +1,181 @@
+// Internal declarations of libcdgpu (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cdgpu.h"
+
+namespace cd {
+
+typedef __int128 i128;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int32_t EMPTY = -1;        // empty hash slot (labels are >= 0)
+constexpr int32_t NOCAND = INT32_MAX;  // "no candidate" community id
+
+// Degree bins of the scan (degree = row length, loops included).
+enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLOCK, B_HUB, NBINS };
+constexpr int WARP_MAX = 256;    // warp per vertex, shared-memory table <= 512 slots
+constexpr int WARP_CAP = 512;
+constexpr int BLOCK_MAX = 4096;  // CTA per vertex, shared-memory table <= 8192 slots
+constexpr int BLOCK_CAP = 8192;
+constexpr int HUB_CHUNK = 16384; // arcs per hub-insert work item
+constexpr int HUB_SLICE = 8192;  // table slots per hub-evaluate work item
+
+// Weight kinds of the device CSR.
+enum WKind { W_UNIT = 0, W_I32 = 1, W_I64 = 2 };
+
+struct WUnit {
+  static constexpr bool unit = true;
+  __device__ __forceinline__ static int64_t get(const void*, int64_t) { return 1; }
+};
+struct WI32 {
+  static constexpr bool unit = false;
+  __device__ __forceinline__ static int64_t get(const void* w, int64_t e) {
+    return (int64_t)__ldg((const int32_t*)w + e);
+  }
+};
+struct WI64 {
+  static constexpr bool unit = false;
+  __device__ __forceinline__ static int64_t get(const void* w, int64_t e) {
+    return (int64_t)__ldg((const long long*)w + e);
+  }
+};
+
+// Counters written by the scan kernels (one int64 each).
+enum Ctr {
+  C_MOVES = 0,   // append cursor of the move list = vertices moved this round
+  C_DEFERRED,    // vertices whose move the coin deferred
+  C_BIN0,        // then per bin: active, arcs, candidates
+  C_COUNT = C_BIN0 + 3 * NBINS
+};
+
+// Per-kernel profiling slots.
+enum Kern {
+  K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLOCK,
+  K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
+  K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+
+}  // namespace cd
+
+// The opaque handle.
+struct cd_graph {
+  cudaStream_t stream = nullptr;
+  int64_t n = 0, nnz = 0, vol = 0, n_isolated = 0;
+  int64_t* off = nullptr;   // n+1
+  int32_t* cols = nullptr;  // nnz
+  void* w = nullptr;        // nnz (int32 or int64), loop arcs carry 2L; null = unit
+  int wkind = cd::W_UNIT;
+  int64_t* degw = nullptr;  // n
+
+  // static degree bins
+  int32_t* bin_list = nullptr;           // n vertex ids grouped by bin
+  int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
+  // hubs (degree > BLOCK_MAX): global hash tables, work items
+  int64_t nhubs = 0, hub_slots = 0, hub_insert_items = 0, hub_eval_items = 0;
+  int64_t* hub_tab = nullptr;      // nhubs+1 slot offsets (caps are powers of two)
+  int32_t* hub_keys = nullptr;     // hub_slots
+  int64_t* hub_vals = nullptr;     // hub_slots
+  int32_t* hub_ins_hub = nullptr;  // per insert item: hub index
+  int64_t* hub_ins_arc = nullptr;  // per insert item: first arc
+  int32_t* hub_ev_hub = nullptr;   // per evaluate item: hub index
+  int64_t* hub_ev_slot = nullptr;  // per evaluate item: first slot
+  int64_t* hub_ev_first = nullptr; // nhubs+1: first evaluate item of each hub
+  int64_t* hub_part = nullptr;     // per evaluate item: 3 words (key hi, key lo, community)
+  int64_t* hub_cur = nullptr;      // nhubs: weight into the hub's own label
+  int32_t* hub_hascur = nullptr;   // nhubs
+  int32_t* hub_done = nullptr;     // nhubs
+
+  // run state (allocated on first use)
+  int32_t* C = nullptr;
+  int64_t* sigma = nullptr;
+  int32_t* csize = nullptr;
+  uint8_t* flag[2] = {nullptr, nullptr};
+  int32_t* mv_v = nullptr;
+  int32_t* mv_c = nullptr;
+  int64_t* ctr = nullptr;      // device counters
+  int64_t* h_ctr = nullptr;    // pinned host copy
+  int32_t* status = nullptr;   // device status word (0 = ok)
+
+  std::vector<cd_round_trace> trace;
+  cd_kernel_profile prof[cd::K_COUNT] = {};
+  bool timing = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;  // (kernel, events)
+  std::vector<double> pending_bytes;
+};
+
+namespace cd {
+
+// error plumbing
+int set_cuda_error(cudaError_t e);
+#define CD_CHECK(call)                                  \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return ::cd::set_cuda_error(_e); \
+  } while (0)
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+template <class T>
+int dev_alloc_t(T** p, int64_t count, cudaStream_t s) {
+  return dev_alloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
+}
+
+// profiling helpers: bracket a launch with events when timing is on
+struct KTimer {
+  cd_graph* g;
+  int k;
+  double bytes;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KTimer(cd_graph* g_, int k_, double bytes_ = 0.0);
+  ~KTimer();
+};
+void profile_reset(cd_graph* g);
+int profile_flush(cd_graph* g);  // syncs, accumulates pending events
+
+// graph.cu
+// Takes ownership of device arrays in the internal convention (loop arcs 2L).
+int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* cols, void* w,
+                int wkind, cd_graph** out, int64_t* degw_pre = nullptr,
+                const unsigned long long* stats_pre = nullptr);
+int ensure_run_state(cd_graph* g);
+int check_labels(cd_graph* g, const int32_t* labels_dev);  // CD_EINVAL if out of [0, n)
+
+// scan.cu
+struct RunOpts {
+  int32_t max_iter;
+  int64_t threshold;  // LPA only
+  int tie_keep_current, singleton_rule, use_frontier;
+  uint64_t sched_seed;
+  int32_t level;
+};
+// Algorithm 1 / Algorithm 2 round loops on g->C (device). Louvain: g->C holds
+// the initial partition; sigma/csize are rebuilt from it.
+int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out);
+int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves_out,
+                   int32_t* rounds_out);
+RunOpts opts_from(const cd_params* p, int32_t level);
+int begin_run(cd_graph* g, const cd_params* p);  // validates params, resets trace/profile
+
+// aggregate.cu
+int renumber(cd_graph* g, const int32_t* labels_dev, int32_t* newid_dev, int64_t* k_out);
+int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, int64_t k,
+              cd_graph** coarse_out);
+int modularity(cd_graph* g, const int32_t* labels_dev, double* q_out);
+
+// prims.cu: device-wide primitives on the graph's stream
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total_dev,
+                       cudaStream_t s);
+int exclusive_scan_u8_to_i32(const uint8_t* in, int32_t* out, int64_t n, int64_t* total_dev,
+                             cudaStream_t s);
+// out[i] = number of run starts (keys[j] != keys[j-1]) among j < i.
+int exclusive_scan_head(const uint64_t* keys, int64_t* out, int64_t n, int64_t* total_dev,
+                        cudaStream_t s);
+int radix_sort_pairs(uint64_t* keys, int64_t* vals, uint64_t* keys_tmp, int64_t* vals_tmp,
+                     int64_t n, int bits, cudaStream_t s, uint64_t** keys_out, int64_t** vals_out);
+
+}  // namespace cd

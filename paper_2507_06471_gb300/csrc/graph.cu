@@ -1,0 +1,647 @@
+// Graph ingest (Sec. II-A): device copy of a symmetric CSR, validation,
+// weighted degrees deg_w(v) (loops counted twice) and vol(V); static degree
+// bins for the scan kernels and the global hash tables of hub vertices.
+//
+// Internal weight convention: a loop arc v->v carries 2L, so that deg_w(v) is
+// the plain row sum and aggregation/modularity sum arc weights without special
+// cases. Upload doubles loop arcs; cd_graph_download halves them back.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace cd {
+
+const char* const kKernelNames[K_COUNT] = {
+    "ingest",      "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32",
+    "scan_warp",   "scan_block", "hub_insert", "hub_eval",    "apply_moves",
+    "renumber",    "agg_emit",   "radix_sort", "agg_reduce",  "modularity"};
+
+static thread_local int g_last_cuda = 0;
+
+int set_cuda_error(cudaError_t e) {
+  g_last_cuda = (int)e;
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return CD_ENOMEM;
+  }
+  return CD_ECUDA;
+}
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  static bool pool_set = false;
+  if (!pool_set) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    pool_set = true;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return set_cuda_error(e);
+  }
+  return CD_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+KTimer::KTimer(cd_graph* g_, int k_, double bytes_) : g(g_), k(k_), bytes(bytes_) {
+  if (g && g->timing) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, g->stream);
+  }
+}
+
+KTimer::~KTimer() {
+  if (g && g->timing) {
+    cudaEventRecord(b, g->stream);
+    g->pending.push_back({k, {a, b}});
+    g->pending_bytes.push_back(bytes);
+  }
+}
+
+void profile_reset(cd_graph* g) {
+  for (int k = 0; k < K_COUNT; ++k) {
+    memset(&g->prof[k], 0, sizeof(cd_kernel_profile));
+    snprintf(g->prof[k].name, sizeof(g->prof[k].name), "%s", kKernelNames[k]);
+  }
+}
+
+int profile_flush(cd_graph* g) {
+  if (g->pending.empty()) return CD_OK;
+  CD_CHECK(cudaStreamSynchronize(g->stream));
+  for (size_t i = 0; i < g->pending.size(); ++i) {
+    auto& p = g->pending[i];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    cd_kernel_profile& kp = g->prof[p.first];
+    kp.launches += 1;
+    kp.total_ms += ms;
+    kp.alg_bytes += g->pending_bytes[i];
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  g->pending.clear();
+  g->pending_bytes.clear();
+  return CD_OK;
+}
+
+namespace {
+
+constexpr int NT = 256;
+
+__device__ __forceinline__ void fail(int32_t* status, int code) { atomicCAS(status, 0, code); }
+
+__device__ __forceinline__ int bin_of(int64_t d) {
+  if (d <= 4) return B_T4;
+  if (d <= 8) return B_T8;
+  if (d <= 16) return B_T16;
+  if (d <= 32) return B_T32;
+  if (d <= WARP_MAX) return B_WARP;
+  if (d <= BLOCK_MAX) return B_BLOCK;
+  return B_HUB;
+}
+
+template <class OffT>
+__global__ void k_offsets_check(const OffT* __restrict__ in, int64_t n, int64_t nnz,
+                                int64_t* __restrict__ out, int32_t* status) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+    int64_t a = (int64_t)in[i];
+    out[i] = a;
+    if (a < 0 || a > nnz) fail(status, CD_ENOTSYM);
+    if (i < n && (int64_t)in[i + 1] < a) fail(status, CD_ENOTSYM);
+    if (i == 0 && a != 0) fail(status, CD_ENOTSYM);
+    if (i == n && a != nnz) fail(status, CD_ENOTSYM);
+  }
+}
+
+// Warp per vertex: bounds-check columns and weights, deg_w with loops twice,
+// loop count, vol(V), per-bin vertex counts. stats: [0] vol, [1] loops,
+// [2] isolated, [3..3+NBINS) bin counts.
+template <class W>
+__global__ void __launch_bounds__(NT) k_ingest(const int64_t* __restrict__ off,
+                                               const int32_t* __restrict__ cols, const void* w,
+                                               int64_t n, int loops_twice, int64_t* __restrict__ degw,
+                                               unsigned long long* stats, int32_t* status) {
+  __shared__ unsigned long long sb[NBINS + 3];
+  if (threadIdx.x < NBINS + 3) sb[threadIdx.x] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_vol = 0, my_loops = 0;
+  for (int64_t v = warp; v < n; v += nwarps) {
+    int64_t beg = off[v], end = off[v + 1];
+    int64_t s = 0, loops = 0;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      int32_t u = cols[e];
+      int64_t x = W::get(w, e);
+      if (u < 0 || u >= n) fail(status, CD_EBOUNDS);
+      if (x < 1) fail(status, CD_EINVAL);
+      s += x;
+      if (u == v) {
+        if (loops_twice) s += x;  // input convention: the loop arc carries L
+        ++loops;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(FULL, s, o);
+      loops += __shfl_xor_sync(FULL, loops, o);
+    }
+    if (lane == 0) {
+      degw[v] = s;
+      my_vol += (unsigned long long)s;
+      my_loops += (unsigned long long)loops;
+      int64_t d = end - beg;
+      if (d == 0)
+        atomicAdd(&sb[2], 1ull);
+      else
+        atomicAdd(&sb[3 + bin_of(d)], 1ull);
+    }
+  }
+  if (lane == 0) {
+    atomicAdd(&sb[0], my_vol);
+    atomicAdd(&sb[1], my_loops);
+  }
+  __syncthreads();
+  if (threadIdx.x < NBINS + 3 && sb[threadIdx.x]) atomicAdd(&stats[threadIdx.x], sb[threadIdx.x]);
+}
+
+// Internal weights with loop arcs doubled (int64).
+template <class W>
+__global__ void __launch_bounds__(NT) k_double_loops(const int64_t* __restrict__ off,
+                                                     const int32_t* __restrict__ cols,
+                                                     const void* w, int64_t n,
+                                                     int64_t* __restrict__ w64) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps)
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+      int64_t x = W::get(w, e);
+      w64[e] = cols[e] == v ? 2 * x : x;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off, int64_t n,
+                                                 const int64_t* __restrict__ bin_base,
+                                                 unsigned long long* cursor,
+                                                 int32_t* __restrict__ list) {
+  const int lane = threadIdx.x & 31;
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t start = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t limit = (n + 31) / 32 * 32;  // whole warps iterate together
+  for (int64_t v = start; v < limit; v += stride) {
+    int b = -1;
+    if (v < n) {
+      int64_t d = off[v + 1] - off[v];
+      if (d > 0) b = bin_of(d);
+    }
+#pragma unroll
+    for (int bb = 0; bb < NBINS; ++bb) {
+      unsigned m = __ballot_sync(FULL, b == bb);
+      if (!m) continue;
+      unsigned long long pos = 0;
+      int first = __ffs(m) - 1;
+      if (lane == first) pos = atomicAdd(&cursor[bb], (unsigned long long)__popc(m));
+      pos = __shfl_sync(FULL, pos, first);
+      if (b == bb) list[bin_base[bb] + (int64_t)pos + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+__global__ void k_gather_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ vs,
+                              int64_t m, int64_t* __restrict__ out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < m) {
+    int32_t v = vs[i];
+    out[2 * i] = off[v];
+    out[2 * i + 1] = off[v + 1];
+  }
+}
+
+__global__ void k_download_w(const int64_t* __restrict__ off, const int32_t* __restrict__ cols,
+                             const void* w, int wkind, int64_t n, int64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t v = warp; v < n; v += nwarps)
+    for (int64_t e = off[v] + lane; e < off[v + 1]; e += 32) {
+      int64_t x = wkind == W_UNIT ? 1 : wkind == W_I32 ? (int64_t)((const int32_t*)w)[e]
+                                                       : ((const int64_t*)w)[e];
+      out[e] = cols[e] == v ? x / 2 : x;  // loop arcs are stored doubled (2L)
+    }
+}
+
+__global__ void k_labels_check(const int32_t* __restrict__ lab, int64_t n, int32_t* status) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    if (lab[i] < 0 || lab[i] >= n) fail(status, CD_EINVAL);
+}
+
+unsigned grid_for(int64_t work, int per_block = NT) {
+  int64_t b = (work + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > 152 * 32) b = 152 * 32;
+  return (unsigned)b;
+}
+
+int read_status(cd_graph* g) {
+  int32_t st = 0;
+  CD_CHECK(cudaMemcpyAsync(&st, g->status, sizeof(int32_t), cudaMemcpyDeviceToHost, g->stream));
+  CD_CHECK(cudaStreamSynchronize(g->stream));
+  if (st) CD_CHECK(cudaMemsetAsync(g->status, 0, sizeof(int32_t), g->stream));
+  return st;
+}
+
+void free_arrays(cd_graph* g) {
+  cudaStream_t s = g->stream;
+  void* ps[] = {g->off,         g->cols,       g->w,           g->degw,        g->bin_list,
+                g->hub_tab,     g->hub_keys,   g->hub_vals,    g->hub_ins_hub, g->hub_ins_arc,
+                g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first, g->hub_part,  g->hub_cur,
+                g->hub_hascur,  g->hub_done,   g->C,           g->sigma,       g->csize,
+                g->flag[0],     g->flag[1],    g->mv_v,        g->mv_c,        g->ctr,
+                g->status};
+  for (void* p : ps) dev_free(p, s);
+  if (g->h_ctr) cudaFreeHost(g->h_ctr);
+}
+
+// Bins, hub tables and status word of a graph whose CSR, weights and deg_w
+// are in place; stats from k_ingest.
+int finish_graph(cd_graph* g, const unsigned long long* stats) {
+  cudaStream_t s = g->stream;
+  g->vol = (int64_t)stats[0];
+  g->n_isolated = (int64_t)stats[2];
+  if (stats[0] >= (1ull << 62)) return CD_EOVERFLOW;
+  g->bin_start[0] = 0;
+  for (int b = 0; b < NBINS; ++b) g->bin_start[b + 1] = g->bin_start[b] + (int64_t)stats[3 + b];
+  int64_t listed = g->bin_start[NBINS];
+  int rc = dev_alloc_t(&g->bin_list, listed, s);
+  if (rc) return rc;
+  int64_t* d_base = nullptr;
+  unsigned long long* d_cur = nullptr;
+  if ((rc = dev_alloc_t(&d_base, NBINS, s))) return rc;
+  if ((rc = dev_alloc_t(&d_cur, NBINS, s))) return rc;
+  CD_CHECK(cudaMemcpyAsync(d_base, g->bin_start, NBINS * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CD_CHECK(cudaMemsetAsync(d_cur, 0, NBINS * sizeof(unsigned long long), s));
+  if (g->n > 0) k_bin_fill<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, d_base, d_cur, g->bin_list);
+  CD_CHECK(cudaGetLastError());
+  // hubs: host-side layout of tables and work items
+  int64_t nh = g->bin_start[B_HUB + 1] - g->bin_start[B_HUB];
+  g->nhubs = nh;
+  if (nh > 0) {
+    int64_t* d_rows = nullptr;
+    if ((rc = dev_alloc_t(&d_rows, 2 * nh, s))) return rc;
+    k_gather_rows<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, g->bin_list + g->bin_start[B_HUB],
+                                                              nh, d_rows);
+    std::vector<int64_t> rows(2 * nh);
+    CD_CHECK(cudaMemcpyAsync(rows.data(), d_rows, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CD_CHECK(cudaStreamSynchronize(s));
+    dev_free(d_rows, s);
+    std::vector<int64_t> tab(nh + 1, 0), ev_first(nh + 1, 0), ins_arc, ev_slot;
+    std::vector<int32_t> ins_hub, ev_hub;
+    for (int64_t h = 0; h < nh; ++h) {
+      int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
+      int64_t cap = deg + deg / 2 + 1;  // load factor <= 2/3 even if every label differs
+      tab[h + 1] = tab[h] + cap;
+      for (int64_t a = 0; a < deg; a += HUB_CHUNK) {
+        ins_hub.push_back((int32_t)h);
+        ins_arc.push_back(beg + a);
+      }
+      ev_first[h] = (int64_t)ev_hub.size();
+      for (int64_t sl = 0; sl < cap; sl += HUB_SLICE) {
+        ev_hub.push_back((int32_t)h);
+        ev_slot.push_back(sl);
+      }
+    }
+    ev_first[nh] = (int64_t)ev_hub.size();
+    g->hub_slots = tab[nh];
+    g->hub_insert_items = (int64_t)ins_hub.size();
+    g->hub_eval_items = (int64_t)ev_hub.size();
+    if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_keys, g->hub_slots, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_vals, g->hub_slots, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ins_hub, g->hub_insert_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ins_arc, g->hub_insert_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ev_hub, g->hub_eval_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ev_slot, g->hub_eval_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ev_first, nh + 1, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_part, 3 * g->hub_eval_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_cur, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_hascur, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_done, nh, s))) return rc;
+    CD_CHECK(cudaMemcpyAsync(g->hub_tab, tab.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ins_hub, ins_hub.data(), ins_hub.size() * 4, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ins_arc, ins_arc.data(), ins_arc.size() * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ev_hub, ev_hub.data(), ev_hub.size() * 4, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ev_slot, ev_slot.data(), ev_slot.size() * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ev_first, ev_first.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_keys, 0xff, g->hub_slots * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_vals, 0, g->hub_slots * 8, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
+    CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
+  }
+  dev_free(d_base, s);
+  dev_free(d_cur, s);
+  return CD_OK;
+}
+
+int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
+  cudaStream_t s = g->stream;
+  unsigned long long* d_stats = nullptr;
+  int rc = dev_alloc_t(&d_stats, NBINS + 3, s);
+  if (rc) return rc;
+  CD_CHECK(cudaMemsetAsync(d_stats, 0, (NBINS + 3) * sizeof(unsigned long long), s));
+  {
+    KTimer t(g, K_UPLOAD, (double)g->nnz * (4 + (g->wkind == W_I32 ? 4 : g->wkind == W_I64 ? 8 : 0)) +
+                              (double)g->n * 16);
+    if (g->n > 0) {
+      unsigned gr = grid_for(g->n * 32);
+      if (g->wkind == W_UNIT)
+        k_ingest<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                         g->status);
+      else if (g->wkind == W_I32)
+        k_ingest<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                        g->status);
+      else
+        k_ingest<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                        g->status);
+    }
+  }
+  CD_CHECK(cudaGetLastError());
+  CD_CHECK(cudaMemcpyAsync(stats_host, d_stats, (NBINS + 3) * sizeof(unsigned long long),
+                           cudaMemcpyDeviceToHost, s));
+  dev_free(d_stats, s);
+  CD_CHECK(cudaStreamSynchronize(s));
+  return CD_OK;
+}
+
+}  // namespace
+
+int ensure_run_state(cd_graph* g) {
+  if (g->C) return CD_OK;
+  cudaStream_t s = g->stream;
+  int rc;
+  if ((rc = dev_alloc_t(&g->C, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->sigma, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->csize, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->flag[0], g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->flag[1], g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->mv_v, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->mv_c, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->ctr, C_COUNT, s))) return rc;
+  if (!g->h_ctr) CD_CHECK(cudaMallocHost(&g->h_ctr, C_COUNT * sizeof(int64_t)));
+  return CD_OK;
+}
+
+int check_labels(cd_graph* g, const int32_t* labels_dev) {
+  if (g->n == 0) return CD_OK;
+  k_labels_check<<<grid_for(g->n), NT, 0, g->stream>>>(labels_dev, g->n, g->status);
+  CD_CHECK(cudaGetLastError());
+  int st = read_status(g);
+  return st ? st : CD_OK;
+}
+
+// Takes ownership of device arrays already in the internal convention (loop
+// arcs carry 2L). If degw_pre is given (with its ingest stats) it is adopted
+// too; otherwise deg_w is computed as the plain row sum.
+int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* cols, void* w,
+                int wkind, cd_graph** out, int64_t* degw_pre, const unsigned long long* stats_pre) {
+  cd_graph* g = new cd_graph();
+  g->stream = s;
+  g->n = n;
+  g->nnz = nnz;
+  g->off = off;
+  g->cols = cols;
+  g->w = w;
+  g->wkind = wkind;
+  g->degw = degw_pre;
+  profile_reset(g);
+  int rc = dev_alloc_t(&g->status, 1, s);
+  if (!rc && cudaMemsetAsync(g->status, 0, 4, s) != cudaSuccess) rc = CD_ECUDA;
+  unsigned long long stats[NBINS + 3] = {};
+  if (stats_pre) {
+    memcpy(stats, stats_pre, sizeof(stats));
+  } else {
+    if (!rc) rc = dev_alloc_t(&g->degw, n, s);
+    if (!rc) rc = ingest(g, 0, stats);
+    if (!rc) {
+      int st = read_status(g);
+      if (st) rc = st;
+    }
+  }
+  if (!rc) rc = finish_graph(g, stats);
+  if (rc) {
+    free_arrays(g);
+    delete g;
+    return rc;
+  }
+  *out = g;
+  return CD_OK;
+}
+
+}  // namespace cd
+
+using namespace cd;
+
+extern "C" {
+
+int cd_params_default(cd_params* p) {
+  if (!p) return CD_EINVAL;
+  p->max_iter = 100;
+  p->max_levels = 64;
+  p->threshold = 0;
+  p->tie_keep_current = 1;
+  p->singleton_rule = 1;
+  p->use_frontier = 1;
+  p->timing = 0;
+  p->sched_seed = 0x5EED5EEDull;
+  return CD_OK;
+}
+
+int cd_last_cuda_error(void) { return g_last_cuda; }
+
+const char* cd_status_string(int st) {
+  switch (st) {
+    case CD_OK: return "ok";
+    case CD_EINVAL: return "invalid argument (null pointer, size, weight < 1 or label out of range)";
+    case CD_EBOUNDS: return "column id outside [0, n)";
+    case CD_ENOMEM: return "device allocation failed";
+    case CD_ECUDA: return "CUDA runtime error";
+    case CD_EOVERFLOW: return "size overflow (vol(V) >= 2^62 or n >= 2^31)";
+    case CD_ETIMEOUT: return "bounded device wait ran out";
+    case CD_ENOTSYM: return "malformed CSR offsets";
+    default: return "unknown status";
+  }
+}
+
+int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols, const int32_t* w,
+                  int64_t n, int64_t nnz, int ptrs_on_device, void* stream, cd_graph** out) {
+  if (!out || n < 0 || nnz < 0 || !offsets || (nnz > 0 && !cols)) return CD_EINVAL;
+  if (n >= (int64_t)INT32_MAX) return CD_EOVERFLOW;
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cd_graph tmp;
+  tmp.stream = s;
+  tmp.n = n;
+  tmp.nnz = nnz;
+  profile_reset(&tmp);
+  int rc = dev_alloc_t(&tmp.status, 1, s);
+  int32_t* d_cols = nullptr;
+  int64_t* d_off = nullptr;
+  int32_t* d_w = nullptr;
+  void* d_off_in = nullptr;
+  if (!rc) rc = dev_alloc_t(&d_off, n + 1, s);
+  if (!rc) rc = dev_alloc_t(&d_cols, nnz, s);
+  if (!rc && w) rc = dev_alloc_t(&d_w, nnz, s);
+  size_t ob = (size_t)(n + 1) * (offsets_is_i64 ? 8 : 4);
+  if (!rc) rc = dev_alloc(&d_off_in, ob, s);
+  auto cleanup = [&]() {
+    dev_free(d_cols, s);
+    dev_free(d_off, s);
+    dev_free(d_w, s);
+    dev_free(d_off_in, s);
+    dev_free(tmp.status, s);
+  };
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  if (cudaMemsetAsync(tmp.status, 0, 4, s) != cudaSuccess ||
+      cudaMemcpyAsync(d_off_in, offsets, ob, kind, s) != cudaSuccess ||
+      (nnz > 0 && cudaMemcpyAsync(d_cols, cols, (size_t)nnz * 4, kind, s) != cudaSuccess) ||
+      (w && nnz > 0 && cudaMemcpyAsync(d_w, w, (size_t)nnz * 4, kind, s) != cudaSuccess)) {
+    int e = set_cuda_error(cudaGetLastError());
+    cleanup();
+    return e;
+  }
+  if (offsets_is_i64)
+    k_offsets_check<int64_t><<<grid_for(n + 1), NT, 0, s>>>((const int64_t*)d_off_in, n, nnz, d_off,
+                                                            tmp.status);
+  else
+    k_offsets_check<int32_t><<<grid_for(n + 1), NT, 0, s>>>((const int32_t*)d_off_in, n, nnz, d_off,
+                                                            tmp.status);
+  int32_t st = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&st, tmp.status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cleanup();
+    return CD_ECUDA;
+  }
+  dev_free(d_off_in, s);
+  d_off_in = nullptr;
+  if (st) {
+    cleanup();
+    return st;
+  }
+  // validate columns and weights, count loops, compute deg_w
+  tmp.off = d_off;
+  tmp.cols = d_cols;
+  tmp.w = d_w;
+  tmp.wkind = d_w ? W_I32 : W_UNIT;
+  rc = dev_alloc_t(&tmp.degw, n, s);
+  unsigned long long stats[NBINS + 3] = {};
+  if (!rc) rc = ingest(&tmp, 1, stats);
+  if (!rc && cudaMemcpyAsync(&st, tmp.status, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess && st)
+    rc = st;
+  dev_free(tmp.status, s);
+  tmp.status = nullptr;
+  if (rc) {
+    dev_free(tmp.degw, s);
+    dev_free(d_cols, s);
+    dev_free(d_off, s);
+    dev_free(d_w, s);
+    return rc;
+  }
+  // loops: switch to int64 weights with loop arcs doubled
+  void* wint = d_w;
+  int wk = d_w ? W_I32 : W_UNIT;
+  if (stats[1] > 0) {
+    int64_t* w64 = nullptr;
+    rc = dev_alloc_t(&w64, nnz, s);
+    if (rc) {
+      dev_free(tmp.degw, s);
+      dev_free(d_cols, s);
+      dev_free(d_off, s);
+      dev_free(d_w, s);
+      return rc;
+    }
+    if (d_w)
+      k_double_loops<WI32><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, d_w, n, w64);
+    else
+      k_double_loops<WUnit><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, nullptr, n, w64);
+    dev_free(d_w, s);
+    wint = w64;
+    wk = W_I64;
+  }
+  return graph_adopt(s, n, nnz, d_off, d_cols, wint, wk, out, tmp.degw, stats);
+}
+
+int cd_graph_free(cd_graph* g) {
+  if (!g) return CD_OK;
+  free_arrays(g);
+  for (auto& p : g->pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  cudaStreamSynchronize(g->stream);
+  delete g;
+  return CD_OK;
+}
+
+int cd_graph_info(const cd_graph* g, int64_t* n, int64_t* nnz, int64_t* vol) {
+  if (!g) return CD_EINVAL;
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (vol) *vol = g->vol;
+  return CD_OK;
+}
+
+int cd_graph_download(const cd_graph* g, int64_t* off, int32_t* cols, int64_t* w, int on_device) {
+  if (!g || !off || (g->nnz > 0 && !cols)) return CD_EINVAL;
+  cudaStream_t s = g->stream;
+  cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CD_CHECK(cudaMemcpyAsync(off, g->off, (g->n + 1) * 8, k, s));
+  if (g->nnz > 0) CD_CHECK(cudaMemcpyAsync(cols, g->cols, g->nnz * 4, k, s));
+  if (w && g->nnz > 0) {
+    int64_t* tmp = nullptr;
+    int rc = dev_alloc_t(&tmp, g->nnz, s);
+    if (rc) return rc;
+    k_download_w<<<grid_for(g->n * 32), NT, 0, s>>>(g->off, g->cols, g->w, g->wkind, g->n, tmp);
+    CD_CHECK(cudaMemcpyAsync(w, tmp, g->nnz * 8, k, s));
+    dev_free(tmp, s);
+  }
+  CD_CHECK(cudaStreamSynchronize(s));
+  return CD_OK;
+}
+
+int cd_trace_get(const cd_graph* g, cd_round_trace* out, int32_t cap, int32_t* count) {
+  if (!g || !count) return CD_EINVAL;
+  *count = (int32_t)g->trace.size();
+  for (int32_t i = 0; i < cap && i < (int32_t)g->trace.size(); ++i) out[i] = g->trace[i];
+  return CD_OK;
+}
+
+int cd_profile_get(const cd_graph* g, cd_kernel_profile* out, int32_t cap, int32_t* count) {
+  if (!g || !count) return CD_EINVAL;
+  *count = K_COUNT;
+  for (int32_t i = 0; i < cap && i < K_COUNT; ++i) out[i] = g->prof[i];
+  return CD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,1005 @@
+// The neighbour-community scan and the synchronous round loops of
+// Label Propagation (Algorithm 1, PLPMove) and Louvain local moving
+// (Algorithm 2, gain of Eq. deltaQ).
+//
+// Per examined vertex v the scan accumulates, for every community c among v's
+// neighbours (loops excluded), k_{v,c} = sum of w(v,u) over u in N(v) with
+// C[u] = c, and picks
+//   LPA:     the c of largest k_{v,c}; the current label is kept if it
+//            attains the maximum (tie_keep_current), else the smallest c;
+//   Louvain: the c != A = C[v] of largest g(c) = vol(V) k_{v,c} - deg_w(v)
+//            Sigma_tot[c] (smallest c on ties) and moves iff
+//            G = g(c) - vol(V) k_{v,A} + deg_w(v) (Sigma_tot[A] - deg_w(v)) > 0,
+//            where G = dQ_{v->c} vol(V)^2 / 2 (Eq. deltaQ, exact in 128 bits).
+// A vertex whose decision differs from its label commits only if the pinned
+// SplitMix64 coin says so; otherwise it defers and stays active.
+//
+// Degree bins (static per graph): degrees 1-4/5-8/9-16/17-32 use TILE lanes
+// per vertex and group equal labels with __match_any_sync; 33-256 a warp with
+// a shared-memory open-addressing table; 257-4096 a CTA with a shared-memory
+// table; larger degrees (hubs) insert into per-hub global tables from many
+// CTAs, then many CTAs evaluate slices of the table and the last one decides.
+#include "common.cuh"
+
+namespace cd {
+namespace {
+
+constexpr int NT = 256;          // threads of tile / warp / hub kernels
+constexpr int NT_BLOCK = 512;    // threads of the CTA-per-vertex kernel
+constexpr int NW = NT / 32;
+constexpr int NW_BLOCK = NT_BLOCK / 32;
+
+// ------------------------------------------------------------------ coin
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): draw number ctr of the
+// stream with state `seed`; the move commits iff bit 63 is set.
+__device__ __forceinline__ bool commit_coin(uint64_t seed, int level, int round, int32_t v) {
+  uint64_t ctr = ((uint64_t)(uint32_t)level << 48) | ((uint64_t)(uint32_t)round << 32) | (uint32_t)v;
+  uint64_t z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (z >> 63) != 0;
+}
+
+// ------------------------------------------------------------------ keys
+
+template <bool LOUV> struct KeyOf { typedef int64_t T; };
+template <> struct KeyOf<true> { typedef i128 T; };
+
+__device__ __forceinline__ int64_t shfl_xor_key(int64_t x, int o) {
+  return __shfl_xor_sync(FULL, (long long)x, o);
+}
+__device__ __forceinline__ i128 shfl_xor_key(i128 x, int o) {
+  unsigned long long lo = (unsigned long long)x, hi = (unsigned long long)(x >> 64);
+  lo = __shfl_xor_sync(FULL, lo, o);
+  hi = __shfl_xor_sync(FULL, hi, o);
+  return (i128)(((unsigned __int128)hi << 64) | lo);
+}
+
+// Is candidate (k1, c1) preferred over (k0, c0)? Larger key, then smaller id.
+template <class K>
+__device__ __forceinline__ bool better(K k1, int32_t c1, K k0, int32_t c0) {
+  if (c1 == NOCAND) return false;
+  if (c0 == NOCAND) return true;
+  return k1 > k0 || (k1 == k0 && c1 < c0);
+}
+
+template <class K>
+__device__ __forceinline__ void reduce_best(K& k, int32_t& c, int width) {
+  for (int o = width / 2; o > 0; o >>= 1) {
+    K ok = shfl_xor_key(k, o);
+    int32_t oc = __shfl_xor_sync(FULL, c, o);
+    if (better(ok, oc, k, c)) {
+      k = ok;
+      c = oc;
+    }
+  }
+}
+
+struct ScanCtx {
+  const int64_t* off;
+  const int32_t* cols;
+  const void* w;
+  const int64_t* degw;
+  int64_t vol;
+  const int32_t* C;
+  const int64_t* sigma;
+  const int32_t* csize;
+  const uint8_t* flag_cur;
+  uint8_t* flag_nxt;
+  int all_active;
+  int mark;  // maintain the next-round flags (frontier on)
+  int32_t* mv_v;
+  int32_t* mv_c;
+  unsigned long long* ctr;
+  int32_t* status;
+  uint64_t seed;
+  int level, round, tie_keep, singleton_rule;
+  // hubs
+  const int32_t* hub_list;
+  const int64_t* hub_tab;
+  int32_t* hub_keys;
+  int64_t* hub_vals;
+  const int32_t* hub_ins_hub;
+  const int64_t* hub_ins_arc;
+  const int32_t* hub_ev_hub;
+  const int64_t* hub_ev_slot;
+  const int64_t* hub_ev_first;
+  int64_t* hub_part;
+  int64_t* hub_cur;
+  int32_t* hub_hascur;
+  int32_t* hub_done;
+  uint8_t* hub_moved;
+  int64_t n_ins_items, n_ev_items;
+};
+
+template <bool LOUV>
+__device__ __forceinline__ typename KeyOf<LOUV>::T cand_key(const ScanCtx& s, int32_t c, int64_t k,
+                                                            int64_t d) {
+  if constexpr (LOUV)
+    return (i128)s.vol * k - (i128)d * s.sigma[c];
+  else
+    return k;
+}
+
+// Final decision of vertex v from the best candidate.
+template <bool LOUV>
+__device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t cur,
+                                          typename KeyOf<LOUV>::T bk, int32_t bc, bool has_cur,
+                                          int64_t kcur) {
+  if (bc == NOCAND) return cur;
+  if constexpr (!LOUV) {
+    if (s.tie_keep && has_cur && kcur == bk) return cur;
+    return bc;
+  } else {
+    int64_t d = s.degw[v];
+    i128 G = bk - (i128)s.vol * kcur + (i128)d * (s.sigma[cur] - d);
+    if (G <= 0) return cur;  // only strictly positive gains
+    if (s.singleton_rule && s.csize[cur] == 1 && s.csize[bc] == 1 && bc > cur) return cur;
+    return bc;
+  }
+}
+
+// One thread acts on a decision: append a committed move or count a deferral.
+// Returns 1 if the move was deferred.
+__device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t cur, int32_t target) {
+  if (target == cur) return 0;
+  if (s.mark) s.flag_nxt[v] = 1;
+  if (commit_coin(s.seed, s.level, s.round, v)) {
+    unsigned long long pos = atomicAdd(&s.ctr[C_MOVES], 1ull);
+    s.mv_v[pos] = v;
+    s.mv_c[pos] = target;
+    return 0;
+  }
+  return 1;
+}
+
+__device__ __forceinline__ void flush_counters(const ScanCtx& s, int bin, int64_t act, int64_t arcs,
+                                               int64_t cands, int64_t def) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    act += __shfl_xor_sync(FULL, act, o);
+    arcs += __shfl_xor_sync(FULL, arcs, o);
+    cands += __shfl_xor_sync(FULL, cands, o);
+    def += __shfl_xor_sync(FULL, def, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (act) atomicAdd(&s.ctr[C_BIN0 + 3 * bin], (unsigned long long)act);
+    if (arcs) atomicAdd(&s.ctr[C_BIN0 + 3 * bin + 1], (unsigned long long)arcs);
+    if (cands) atomicAdd(&s.ctr[C_BIN0 + 3 * bin + 2], (unsigned long long)cands);
+    if (def) atomicAdd(&s.ctr[C_DEFERRED], (unsigned long long)def);
+  }
+}
+
+__device__ __forceinline__ bool is_active(const ScanCtx& s, int32_t v) {
+  return s.all_active || s.flag_cur[v];
+}
+
+// Group weight of the lanes in `peers` (equal labels): popcount for unit
+// weights, else a sum over the warp's staging row.
+template <class W>
+__device__ __forceinline__ int64_t group_sum(unsigned peers, int64_t wt, int64_t* stage) {
+  if constexpr (W::unit) {
+    return (int64_t)__popc(peers);
+  } else {
+    const int lane = threadIdx.x & 31;
+    stage[lane] = wt;
+    __syncwarp();
+    int64_t s = 0;
+    unsigned m = peers;
+    while (m) {
+      s += stage[__ffs(m) - 1];
+      m &= m - 1;
+    }
+    __syncwarp();
+    return s;
+  }
+}
+
+// ------------------------------------------------------------------ tiles
+
+// TILE lanes per vertex, one arc per lane (degree <= TILE).
+template <int TILE, bool LOUV, class W>
+__global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __restrict__ list,
+                                                  int64_t count, int bin) {
+  typedef typename KeyOf<LOUV>::T K;
+  __shared__ int64_t stage[NW][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int sub = lane & (TILE - 1);
+  const int tbase = lane & ~(TILE - 1);
+  const unsigned tmask = TILE == 32 ? FULL : (((1u << TILE) - 1u) << tbase);
+  constexpr int VPW = 32 / TILE;
+  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  for (int64_t base = warp * VPW; base < count; base += nwarps * VPW) {
+    const int64_t i = base + lane / TILE;
+    const bool valid = i < count;
+    const int32_t v = valid ? list[i] : 0;
+    const bool act = valid && is_active(s, v);
+    int64_t beg = 0;
+    int d = 0;
+    if (act) {
+      beg = s.off[v];
+      d = (int)(s.off[v + 1] - beg);
+    }
+    const bool has = act && sub < d;
+    const int32_t u = has ? s.cols[beg + sub] : v;
+    const int64_t wt = has ? W::get(s.w, beg + sub) : 0;
+    const bool cand = has && u != v;
+    const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
+    const unsigned peers = __match_any_sync(FULL, lbl) & tmask;
+    const int64_t gsum = group_sum<W>(peers, wt, stage[wid]);
+    const bool leader = cand && (__ffs(peers) - 1) == lane;
+    const int32_t cur = act ? s.C[v] : 0;
+    const unsigned cm = __ballot_sync(FULL, cand && lbl == cur) & tmask;
+    int64_t kcur = __shfl_sync(FULL, gsum, cm ? __ffs(cm) - 1 : lane);
+    if (!cm) kcur = 0;
+    const int64_t dv = (LOUV && act) ? s.degw[v] : 0;
+    const bool ok = leader && (!LOUV || lbl != cur);
+    K bk = ok ? cand_key<LOUV>(s, lbl, gsum, dv) : K(0);
+    int32_t bc = ok ? lbl : NOCAND;
+    reduce_best(bk, bc, TILE);
+    int32_t target = cur;
+    if (act) target = decide<LOUV>(s, v, cur, bk, bc, cm != 0, kcur);
+    const bool want = act && target != cur;
+    const bool commit = want && commit_coin(s.seed, s.level, s.round, v);
+    const unsigned am = __ballot_sync(FULL, commit && sub == 0);
+    if (am) {
+      const int first = __ffs(am) - 1;
+      unsigned long long pos0 = 0;
+      if (lane == first) pos0 = atomicAdd(&s.ctr[C_MOVES], (unsigned long long)__popc(am));
+      pos0 = __shfl_sync(FULL, pos0, first);
+      if (commit && sub == 0) {
+        const unsigned long long pos = pos0 + __popc(am & ((1u << lane) - 1u));
+        s.mv_v[pos] = v;
+        s.mv_c[pos] = target;
+      }
+    }
+    if (s.mark) {
+      if (commit && has) s.flag_nxt[u] = 1;  // the neighbours of a moved vertex
+      if (want && sub == 0) s.flag_nxt[v] = 1;
+    }
+    if (sub == 0 && act) {
+      ++n_act;
+      n_arcs += d;
+      if (want && !commit) ++n_def;
+    }
+    if (ok) ++n_cand;
+  }
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+}
+
+// ------------------------------------------------------------------ shared-memory tables
+
+__device__ __forceinline__ bool smem_insert(int32_t* keys, int64_t* vals, unsigned lg, int32_t key,
+                                            int64_t w, int32_t* status) {
+  const unsigned mask = (1u << lg) - 1u;
+  unsigned h = ((uint32_t)key * 2654435761u) >> (32 - lg);
+  for (unsigned probe = 0; probe <= mask; ++probe) {
+    int32_t prev = atomicCAS(&keys[h], EMPTY, key);
+    if (prev == EMPTY || prev == key) {
+      atomicAdd((unsigned long long*)&vals[h], (unsigned long long)w);
+      return true;
+    }
+    h = (h + 1) & mask;
+  }
+  atomicCAS(status, 0, CD_ETIMEOUT);  // table full: cannot happen with cap >= 2 deg
+  return false;
+}
+
+__device__ __forceinline__ unsigned ceil_log2(int64_t x) {
+  unsigned lg = 0;
+  while (((int64_t)1 << lg) < x) ++lg;
+  return lg;
+}
+
+// Warp per vertex, degree 33..WARP_MAX, table of next_pow2(2 deg) slots.
+template <bool LOUV, class W>
+__global__ void __launch_bounds__(NT) k_scan_warp(ScanCtx s, const int32_t* __restrict__ list,
+                                                  int64_t count, int bin) {
+  typedef typename KeyOf<LOUV>::T K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t* vals = (int64_t*)smem + (size_t)wid * WARP_CAP;
+  int32_t* keys = (int32_t*)(smem + (size_t)NW * WARP_CAP * 8) + (size_t)wid * WARP_CAP;
+  int64_t* stage = (int64_t*)(smem + (size_t)NW * WARP_CAP * 12) + wid * 32;
+  for (int j = lane; j < WARP_CAP; j += 32) {
+    keys[j] = EMPTY;
+    vals[j] = 0;
+  }
+  __syncwarp();
+  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  for (int64_t i = warp; i < count; i += nwarps) {
+    const int32_t v = list[i];
+    if (!is_active(s, v)) continue;  // warp-uniform
+    const int64_t beg = s.off[v], end = s.off[v + 1];
+    const int64_t d = end - beg;
+    const unsigned lg = ceil_log2(2 * d);
+    const int cap = 1 << lg;
+    const int32_t cur = s.C[v];
+    for (int64_t e0 = beg; e0 < end; e0 += 32) {
+      const int64_t e = e0 + lane;
+      const bool has = e < end;
+      const int32_t u = has ? s.cols[e] : v;
+      const int64_t wt = has ? W::get(s.w, e) : 0;
+      const bool cand = has && u != v;
+      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
+      const unsigned peers = __match_any_sync(FULL, lbl);
+      const int64_t gsum = group_sum<W>(peers, wt, stage);
+      if (cand && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl, gsum, s.status);
+    }
+    __syncwarp();
+    const int64_t dv = LOUV ? s.degw[v] : 0;
+    K bk = K(0);
+    int32_t bc = NOCAND;
+    bool hc = false;
+    int64_t kc = 0;
+    for (int j = lane; j < cap; j += 32) {
+      const int32_t c = keys[j];
+      if (c == EMPTY) continue;
+      const int64_t k = vals[j];
+      keys[j] = EMPTY;
+      vals[j] = 0;
+      ++n_cand;
+      if (c == cur) {
+        hc = true;
+        kc = k;
+      }
+      if (LOUV && c == cur) continue;
+      const K key = cand_key<LOUV>(s, c, k, dv);
+      if (better(key, c, bk, bc)) {
+        bk = key;
+        bc = c;
+      }
+    }
+    reduce_best(bk, bc, 32);
+    const unsigned hm = __ballot_sync(FULL, hc);
+    if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
+    __syncwarp();
+    if (lane == 0) {
+      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc);
+      n_def += act_single(s, v, cur, target);
+      ++n_act;
+      n_arcs += d;
+    }
+  }
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+}
+
+// CTA per vertex, degree WARP_MAX+1..BLOCK_MAX.
+template <bool LOUV, class W>
+__global__ void __launch_bounds__(NT_BLOCK) k_scan_block(ScanCtx s, const int32_t* __restrict__ list,
+                                                         int64_t count, int bin) {
+  typedef typename KeyOf<LOUV>::T K;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ K red_k[NW_BLOCK];
+  __shared__ int32_t red_c[NW_BLOCK];
+  __shared__ int64_t s_kcur;
+  __shared__ int s_hascur;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t* vals = (int64_t*)smem;
+  int32_t* keys = (int32_t*)(smem + (size_t)BLOCK_CAP * 8);
+  int64_t* stage = (int64_t*)(smem + (size_t)BLOCK_CAP * 12) + wid * 32;
+  for (int j = threadIdx.x; j < BLOCK_CAP; j += NT_BLOCK) {
+    keys[j] = EMPTY;
+    vals[j] = 0;
+  }
+  if (threadIdx.x == 0) {
+    s_hascur = 0;
+    s_kcur = 0;
+  }
+  __syncthreads();
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const int32_t v = list[i];
+    if (!is_active(s, v)) continue;  // CTA-uniform
+    const int64_t beg = s.off[v], end = s.off[v + 1];
+    const int64_t d = end - beg;
+    const unsigned lg = ceil_log2(2 * d);
+    const int cap = 1 << lg;
+    const int32_t cur = s.C[v];
+    for (int64_t e0 = beg + wid * 32; e0 < end; e0 += NT_BLOCK) {
+      const int64_t e = e0 + lane;
+      const bool has = e < end;
+      const int32_t u = has ? s.cols[e] : v;
+      const int64_t wt = has ? W::get(s.w, e) : 0;
+      const bool cand = has && u != v;
+      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
+      const unsigned peers = __match_any_sync(FULL, lbl);
+      const int64_t gsum = group_sum<W>(peers, wt, stage);
+      if (cand && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl, gsum, s.status);
+    }
+    __syncthreads();
+    const int64_t dv = LOUV ? s.degw[v] : 0;
+    K bk = K(0);
+    int32_t bc = NOCAND;
+    for (int j = threadIdx.x; j < cap; j += NT_BLOCK) {
+      const int32_t c = keys[j];
+      if (c == EMPTY) continue;
+      const int64_t k = vals[j];
+      keys[j] = EMPTY;
+      vals[j] = 0;
+      ++n_cand;
+      if (c == cur) {
+        s_hascur = 1;
+        s_kcur = k;
+      }
+      if (LOUV && c == cur) continue;
+      const K key = cand_key<LOUV>(s, c, k, dv);
+      if (better(key, c, bk, bc)) {
+        bk = key;
+        bc = c;
+      }
+    }
+    reduce_best(bk, bc, 32);
+    if (lane == 0) {
+      red_k[wid] = bk;
+      red_c[wid] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w2 = 1; w2 < NW_BLOCK; ++w2)
+        if (better(red_k[w2], red_c[w2], bk, bc)) {
+          bk = red_k[w2];
+          bc = red_c[w2];
+        }
+      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, s_hascur != 0, s_kcur);
+      n_def += act_single(s, v, cur, target);
+      ++n_act;
+      n_arcs += d;
+      s_hascur = 0;
+      s_kcur = 0;
+    }
+    __syncthreads();
+  }
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+}
+
+// ------------------------------------------------------------------ hubs
+
+__device__ __forceinline__ void global_insert(int32_t* keys, int64_t* vals, int64_t cap, int32_t key,
+                                              int64_t w, int32_t* status) {
+  int64_t h = (int64_t)(((uint64_t)((uint32_t)key * 2654435761u) * (uint64_t)cap) >> 32);
+  for (int64_t probe = 0; probe < cap; ++probe) {
+    int32_t prev = atomicCAS(&keys[h], EMPTY, key);
+    if (prev == EMPTY || prev == key) {
+      atomicAdd((unsigned long long*)&vals[h], (unsigned long long)w);
+      return;
+    }
+    h = h + 1 == cap ? 0 : h + 1;
+  }
+  atomicCAS(status, 0, CD_ETIMEOUT);
+}
+
+// Every CTA item inserts up to HUB_CHUNK arcs of one hub into its table.
+template <class W>
+__global__ void __launch_bounds__(NT) k_hub_insert(ScanCtx s) {
+  __shared__ int64_t stage[NW][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int64_t it = blockIdx.x; it < s.n_ins_items; it += gridDim.x) {
+    const int32_t h = s.hub_ins_hub[it];
+    const int32_t v = s.hub_list[h];
+    if (!is_active(s, v)) continue;
+    const int64_t a0 = s.hub_ins_arc[it];
+    const int64_t rowend = s.off[v + 1];
+    const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
+    int32_t* keys = s.hub_keys + s.hub_tab[h];
+    int64_t* vals = s.hub_vals + s.hub_tab[h];
+    const int64_t cap = s.hub_tab[h + 1] - s.hub_tab[h];
+    for (int64_t e0 = a0 + wid * 32; e0 < end; e0 += NT) {
+      const int64_t e = e0 + lane;
+      const bool has = e < end;
+      const int32_t u = has ? s.cols[e] : v;
+      const int64_t wt = has ? W::get(s.w, e) : 0;
+      const bool cand = has && u != v;
+      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
+      const unsigned peers = __match_any_sync(FULL, lbl);
+      const int64_t gsum = group_sum<W>(peers, wt, stage[wid]);
+      if (cand && (__ffs(peers) - 1) == lane) global_insert(keys, vals, cap, lbl, gsum, s.status);
+    }
+  }
+}
+
+// Every CTA item scans HUB_SLICE slots of one hub's table (and clears them);
+// the last item of a hub to finish reduces the partial results and decides.
+template <bool LOUV>
+__global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s, int bin) {
+  typedef typename KeyOf<LOUV>::T K;
+  __shared__ K red_k[NW];
+  __shared__ int32_t red_c[NW];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  for (int64_t it = blockIdx.x; it < s.n_ev_items; it += gridDim.x) {
+    const int32_t h = s.hub_ev_hub[it];
+    const int32_t v = s.hub_list[h];
+    if (!is_active(s, v)) continue;
+    const int32_t cur = s.C[v];
+    const int64_t dv = LOUV ? s.degw[v] : 0;
+    int32_t* keys = s.hub_keys + s.hub_tab[h];
+    int64_t* vals = s.hub_vals + s.hub_tab[h];
+    const int64_t cap = s.hub_tab[h + 1] - s.hub_tab[h];
+    const int64_t s0 = s.hub_ev_slot[it];
+    const int64_t s1 = s0 + HUB_SLICE < cap ? s0 + HUB_SLICE : cap;
+    K bk = K(0);
+    int32_t bc = NOCAND;
+    for (int64_t j = s0 + threadIdx.x; j < s1; j += NT) {
+      const int32_t c = keys[j];
+      if (c == EMPTY) continue;
+      const int64_t k = vals[j];
+      keys[j] = EMPTY;
+      vals[j] = 0;
+      ++n_cand;
+      if (c == cur) {
+        s.hub_cur[h] = k;
+        s.hub_hascur[h] = 1;
+      }
+      if (LOUV && c == cur) continue;
+      const K key = cand_key<LOUV>(s, c, k, dv);
+      if (better(key, c, bk, bc)) {
+        bk = key;
+        bc = c;
+      }
+    }
+    reduce_best(bk, bc, 32);
+    if (lane == 0) {
+      red_k[wid] = bk;
+      red_c[wid] = bc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w2 = 1; w2 < NW; ++w2)
+        if (better(red_k[w2], red_c[w2], bk, bc)) {
+          bk = red_k[w2];
+          bc = red_c[w2];
+        }
+      i128 kk = (i128)bk;
+      s.hub_part[3 * it] = (int64_t)(kk >> 64);
+      s.hub_part[3 * it + 1] = (int64_t)(uint64_t)kk;
+      s.hub_part[3 * it + 2] = bc;
+      __threadfence();
+      const int64_t first = s.hub_ev_first[h], nparts = s.hub_ev_first[h + 1] - first;
+      s_last = atomicAdd(&s.hub_done[h], 1) == (int)(nparts - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+      __threadfence();
+      const int64_t first = s.hub_ev_first[h], last = s.hub_ev_first[h + 1];
+      const volatile int64_t* part = s.hub_part;
+      K fk = K(0);
+      int32_t fc = NOCAND;
+      for (int64_t p = first; p < last; ++p) {
+        const i128 pk = (i128)(((unsigned __int128)(uint64_t)part[3 * p] << 64) |
+                               (uint64_t)part[3 * p + 1]);
+        const int32_t pc = (int32_t)part[3 * p + 2];
+        if (better((K)pk, pc, fk, fc)) {
+          fk = (K)pk;
+          fc = pc;
+        }
+      }
+      const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
+      const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
+      const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc);
+      const int def = act_single(s, v, cur, target);
+      n_def += def;
+      if (target != cur && !def) s.hub_moved[h] = 1;
+      ++n_act;
+      n_arcs += s.off[v + 1] - s.off[v];
+      s.hub_done[h] = 0;
+      s.hub_cur[h] = 0;
+      s.hub_hascur[h] = 0;
+    }
+    __syncthreads();
+  }
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+}
+
+// ------------------------------------------------------------------ apply
+
+// Warp per committed move: new label, Sigma_tot and community sizes (Louvain),
+// and the next-round flags of the neighbours of vertices with 33..BLOCK_MAX arcs
+// (tile kernels flag their own; hubs are flagged by k_hub_mark).
+template <bool LOUV>
+__global__ void __launch_bounds__(NT) k_apply(const int32_t* __restrict__ mv_v,
+                                              const int32_t* __restrict__ mv_c, int64_t nmoves,
+                                              const int64_t* __restrict__ off,
+                                              const int32_t* __restrict__ cols,
+                                              const int64_t* __restrict__ degw, int32_t* C,
+                                              int64_t* sigma, int32_t* csize, uint8_t* flag_nxt,
+                                              int mark) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  for (int64_t m = warp; m < nmoves; m += nwarps) {
+    const int32_t v = mv_v[m], c = mv_c[m];
+    if (lane == 0) {
+      if (LOUV) {
+        const int32_t A = C[v];
+        const int64_t d = degw[v];
+        atomicAdd((unsigned long long*)&sigma[A], (unsigned long long)(-d));
+        atomicAdd((unsigned long long*)&sigma[c], (unsigned long long)d);
+        atomicSub(&csize[A], 1);
+        atomicAdd(&csize[c], 1);
+      }
+      C[v] = c;
+    }
+    if (mark) {
+      const int64_t beg = off[v], end = off[v + 1];
+      if (end - beg > 32 && end - beg <= BLOCK_MAX)
+        for (int64_t e = beg + lane; e < end; e += 32) flag_nxt[cols[e]] = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
+  for (int64_t it = blockIdx.x; it < s.n_ins_items; it += gridDim.x) {
+    const int32_t h = s.hub_ins_hub[it];
+    if (!s.hub_moved[h]) continue;
+    const int32_t v = s.hub_list[h];
+    const int64_t a0 = s.hub_ins_arc[it];
+    const int64_t rowend = s.off[v + 1];
+    const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
+    for (int64_t e = a0 + threadIdx.x; e < end; e += NT) s.flag_nxt[s.cols[e]] = 1;
+  }
+}
+
+__global__ void k_init_singletons(int32_t* C, int64_t* sigma, int32_t* csize,
+                                  const int64_t* __restrict__ degw, int64_t n, int louv) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    C[v] = (int32_t)v;
+    if (louv) {
+      sigma[v] = degw[v];
+      csize[v] = 1;
+    }
+  }
+}
+
+__global__ void k_init_given(const int32_t* __restrict__ C, int64_t* sigma, int32_t* csize,
+                             const int64_t* __restrict__ degw, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    atomicAdd((unsigned long long*)&sigma[C[v]], (unsigned long long)degw[v]);
+    atomicAdd(&csize[C[v]], 1);
+  }
+}
+
+unsigned grid_cap(int64_t blocks, int64_t cap = 152 * 16) {
+  if (blocks < 1) blocks = 1;
+  return (unsigned)(blocks < cap ? blocks : cap);
+}
+
+size_t warp_smem() { return (size_t)NW * WARP_CAP * 12 + (size_t)NW * 32 * 8; }
+size_t block_smem() { return (size_t)BLOCK_CAP * 12 + (size_t)NW_BLOCK * 32 * 8; }
+
+template <bool LOUV, class W>
+int set_smem_attrs() {
+  static bool done = false;
+  if (done) return CD_OK;
+  CD_CHECK(cudaFuncSetAttribute(k_scan_warp<LOUV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)warp_smem()));
+  CD_CHECK(cudaFuncSetAttribute(k_scan_block<LOUV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)block_smem()));
+  done = true;
+  return CD_OK;
+}
+
+// Algorithmic bytes of one scan launch (per examined vertex: offset, own
+// label, flag; per arc: column, neighbour label, weight; Louvain adds deg_w,
+// Sigma_tot[A], sizes per vertex and one Sigma_tot gather per candidate).
+double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cands) {
+  double b = (double)act * (8 + 4 + 1) + (double)arcs * (4 + 4 + wbytes);
+  if (louv) b += (double)act * (8 + 8 + 8) + (double)cands * 8;
+  return b;
+}
+
+template <bool LOUV, class W>
+int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
+  int rc = set_smem_attrs<LOUV, W>();
+  if (rc) return rc;
+  cudaStream_t st = g->stream;
+  auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
+  auto lst = [&](int b) { return g->bin_list + g->bin_start[b]; };
+  auto mark = [&](int b) { marks.push_back({g->pending.size() - 1, b}); };
+  if (cnt(B_HUB) > 0) {
+    {
+      KTimer t(g, K_HUB_INSERT);
+      k_hub_insert<W><<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s);
+    }
+    if (g->timing) marks.push_back({g->pending.size() - 1, -1});
+    {
+      KTimer t(g, K_HUB_EVAL);
+      k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s, B_HUB);
+    }
+    if (g->timing) mark(B_HUB);
+  }
+  if (cnt(B_BLOCK) > 0) {
+    {
+      KTimer t(g, K_SCAN_BLOCK);
+      k_scan_block<LOUV, W><<<grid_cap(cnt(B_BLOCK), 152 * 4), NT_BLOCK, block_smem(), st>>>(
+          s, lst(B_BLOCK), cnt(B_BLOCK), B_BLOCK);
+    }
+    if (g->timing) mark(B_BLOCK);
+  }
+  if (cnt(B_WARP) > 0) {
+    {
+      KTimer t(g, K_SCAN_WARP);
+      k_scan_warp<LOUV, W><<<grid_cap((cnt(B_WARP) + NW - 1) / NW), NT, warp_smem(), st>>>(
+          s, lst(B_WARP), cnt(B_WARP), B_WARP);
+    }
+    if (g->timing) mark(B_WARP);
+  }
+  if (cnt(B_T32) > 0) {
+    {
+      KTimer t(g, K_SCAN_T32);
+      k_scan_tile<32, LOUV, W><<<grid_cap((cnt(B_T32) + NW - 1) / NW), NT, 0, st>>>(
+          s, lst(B_T32), cnt(B_T32), B_T32);
+    }
+    if (g->timing) mark(B_T32);
+  }
+  if (cnt(B_T16) > 0) {
+    {
+      KTimer t(g, K_SCAN_T16);
+      k_scan_tile<16, LOUV, W><<<grid_cap((cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
+          s, lst(B_T16), cnt(B_T16), B_T16);
+    }
+    if (g->timing) mark(B_T16);
+  }
+  if (cnt(B_T8) > 0) {
+    {
+      KTimer t(g, K_SCAN_T8);
+      k_scan_tile<8, LOUV, W><<<grid_cap((cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
+          s, lst(B_T8), cnt(B_T8), B_T8);
+    }
+    if (g->timing) mark(B_T8);
+  }
+  if (cnt(B_T4) > 0) {
+    {
+      KTimer t(g, K_SCAN_T4);
+      k_scan_tile<4, LOUV, W><<<grid_cap((cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
+          s, lst(B_T4), cnt(B_T4), B_T4);
+    }
+    if (g->timing) mark(B_T4);
+  }
+  CD_CHECK(cudaGetLastError());
+  return CD_OK;
+}
+
+int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out) {
+  cudaStream_t st = g->stream;
+  const int64_t n = g->n;
+  uint8_t* hub_moved = nullptr;
+  int rc = CD_OK;
+  if (g->nhubs > 0 && (rc = dev_alloc_t(&hub_moved, g->nhubs, st))) return rc;
+  uint8_t* fcur = g->flag[0];
+  uint8_t* fnxt = g->flag[1];
+  if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fcur, 1, n, st));
+  const int wbytes = g->wkind == W_UNIT ? 0 : g->wkind == W_I32 ? 4 : 8;
+  int64_t total_moves = 0;
+  int32_t rounds = 0;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (g->timing)
+    for (auto& e : ev) cudaEventCreate(&e);
+  for (int32_t r = 0; r < o.max_iter && rc == CD_OK; ++r) {
+    if (g->timing) cudaEventRecord(ev[0], st);
+    CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
+    if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, n, st));
+    if (hub_moved) CD_CHECK(cudaMemsetAsync(hub_moved, 0, g->nhubs, st));
+    ScanCtx s;
+    s.off = g->off;
+    s.cols = g->cols;
+    s.w = g->w;
+    s.degw = g->degw;
+    s.vol = g->vol;
+    s.C = g->C;
+    s.sigma = g->sigma;
+    s.csize = g->csize;
+    s.flag_cur = fcur;
+    s.flag_nxt = fnxt;
+    s.all_active = o.use_frontier ? 0 : 1;
+    s.mark = o.use_frontier ? 1 : 0;
+    s.mv_v = g->mv_v;
+    s.mv_c = g->mv_c;
+    s.ctr = (unsigned long long*)g->ctr;
+    s.status = g->status;
+    s.seed = o.sched_seed;
+    s.level = o.level;
+    s.round = r;
+    s.tie_keep = o.tie_keep_current;
+    s.singleton_rule = o.singleton_rule;
+    s.hub_list = g->bin_list + g->bin_start[B_HUB];
+    s.hub_tab = g->hub_tab;
+    s.hub_keys = g->hub_keys;
+    s.hub_vals = g->hub_vals;
+    s.hub_ins_hub = g->hub_ins_hub;
+    s.hub_ins_arc = g->hub_ins_arc;
+    s.hub_ev_hub = g->hub_ev_hub;
+    s.hub_ev_slot = g->hub_ev_slot;
+    s.hub_ev_first = g->hub_ev_first;
+    s.hub_part = g->hub_part;
+    s.hub_cur = g->hub_cur;
+    s.hub_hascur = g->hub_hascur;
+    s.hub_done = g->hub_done;
+    s.hub_moved = hub_moved;
+    s.n_ins_items = g->hub_insert_items;
+    s.n_ev_items = g->hub_eval_items;
+    std::vector<std::pair<size_t, int>> marks;
+    if (louv) {
+      if (g->wkind == W_UNIT) rc = launch_round<true, WUnit>(g, s, marks);
+      else if (g->wkind == W_I32) rc = launch_round<true, WI32>(g, s, marks);
+      else rc = launch_round<true, WI64>(g, s, marks);
+    } else {
+      if (g->wkind == W_UNIT) rc = launch_round<false, WUnit>(g, s, marks);
+      else if (g->wkind == W_I32) rc = launch_round<false, WI32>(g, s, marks);
+      else rc = launch_round<false, WI64>(g, s, marks);
+    }
+    if (rc) break;
+    if (g->timing) cudaEventRecord(ev[1], st);
+    CD_CHECK(cudaMemcpyAsync(g->h_ctr, g->ctr, C_COUNT * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CD_CHECK(cudaStreamSynchronize(st));
+    const int64_t* h = g->h_ctr;
+    const int64_t moves = h[C_MOVES], deferred = h[C_DEFERRED];
+    int64_t act = 0, arcs = 0;
+    for (int b = 0; b < NBINS; ++b) {
+      act += h[C_BIN0 + 3 * b];
+      arcs += h[C_BIN0 + 3 * b + 1];
+    }
+    for (auto& mk : marks) {
+      const int b = mk.second;
+      const int64_t ab = b >= 0 ? h[C_BIN0 + 3 * b] : 0;
+      const int64_t rb = h[C_BIN0 + 3 * B_HUB + 1], cb = b >= 0 ? h[C_BIN0 + 3 * b + 2] : 0;
+      double bytes;
+      if (b == -1)  // hub insert: arcs in, one table update per distinct label
+        bytes = (double)rb * (4 + 4 + wbytes) + (double)h[C_BIN0 + 3 * B_HUB + 2] * 12;
+      else if (b == B_HUB)  // hub evaluate: the candidates of every active hub
+        bytes = (double)cb * (12 + 12 + (louv ? 8 : 0)) + (double)ab * (8 + 4);
+      else
+        bytes = scan_bytes(louv, wbytes, ab, h[C_BIN0 + 3 * b + 1], cb);
+      g->pending_bytes[mk.first] = bytes;
+    }
+    if (moves > 0) {
+      KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
+      const unsigned gr = grid_cap((moves + NW - 1) / NW);
+      if (louv)
+        k_apply<true><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
+                                         g->sigma, g->csize, fnxt, s.mark);
+      else
+        k_apply<false><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
+                                          g->sigma, g->csize, fnxt, s.mark);
+      if (hub_moved && s.mark)
+        k_hub_mark<<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s);
+      CD_CHECK(cudaGetLastError());
+    }
+    cd_round_trace tr;
+    tr.level = o.level;
+    tr.round = r;
+    tr.active = act + ((r == 0 || !o.use_frontier) ? g->n_isolated : 0);
+    tr.arcs = arcs;
+    tr.moved = moves;
+    tr.deferred = deferred;
+    tr.scan_ms = tr.round_ms = 0.f;
+    if (g->timing) {
+      cudaEventRecord(ev[2], st);
+      CD_CHECK(cudaEventSynchronize(ev[2]));
+      cudaEventElapsedTime(&tr.scan_ms, ev[0], ev[1]);
+      cudaEventElapsedTime(&tr.round_ms, ev[0], ev[2]);
+    }
+    g->trace.push_back(tr);
+    total_moves += moves;
+    rounds = r + 1;
+    std::swap(fcur, fnxt);
+    const bool stop = louv ? (moves + deferred == 0) : (moves + deferred <= o.threshold);
+    if (stop) break;
+  }
+  if (g->timing)
+    for (auto& e : ev) cudaEventDestroy(e);
+  dev_free(hub_moved, st);
+  if (rc) return rc;
+  int32_t stw = 0;
+  CD_CHECK(cudaMemcpyAsync(&stw, g->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CD_CHECK(cudaStreamSynchronize(st));
+  if (stw) return stw;
+  if (moves_out) *moves_out = total_moves;
+  if (rounds_out) *rounds_out = rounds;
+  return profile_flush(g);
+}
+
+}  // namespace
+
+int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out) {
+  int rc = ensure_run_state(g);
+  if (rc) return rc;
+  if (g->n > 0)
+    k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, g->stream>>>(g->C, g->sigma, g->csize,
+                                                                            g->degw, g->n, 0);
+  CD_CHECK(cudaGetLastError());
+  return run_rounds(g, o, false, nullptr, rounds_out);
+}
+
+int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves_out,
+                   int32_t* rounds_out) {
+  int rc = ensure_run_state(g);
+  if (rc) return rc;
+  cudaStream_t st = g->stream;
+  if (g->n > 0) {
+    if (!init_given) {
+      k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize,
+                                                                       g->degw, g->n, 1);
+    } else {
+      CD_CHECK(cudaMemsetAsync(g->sigma, 0, g->n * sizeof(int64_t), st));
+      CD_CHECK(cudaMemsetAsync(g->csize, 0, g->n * sizeof(int32_t), st));
+      k_init_given<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize, g->degw,
+                                                                  g->n);
+    }
+  }
+  CD_CHECK(cudaGetLastError());
+  return run_rounds(g, o, true, moves_out, rounds_out);
+}
+
+RunOpts opts_from(const cd_params* p, int32_t level) {
+  RunOpts o;
+  o.max_iter = p->max_iter;
+  o.threshold = p->threshold;
+  o.tie_keep_current = p->tie_keep_current;
+  o.singleton_rule = p->singleton_rule;
+  o.use_frontier = p->use_frontier;
+  o.sched_seed = p->sched_seed;
+  o.level = level;
+  return o;
+}
+
+int begin_run(cd_graph* g, const cd_params* p) {
+  if (!g || !p || p->max_iter < 0 || p->max_iter > 65535 || p->max_levels < 0 ||
+      p->max_levels > 32767)
+    return CD_EINVAL;
+  g->timing = p->timing != 0;
+  g->trace.clear();
+  profile_reset(g);
+  return CD_OK;
+}
+
+}  // namespace cd
+
+using namespace cd;
+
+extern "C" {
+
+int cd_lpa_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
+               int32_t* rounds_out) {
+  int rc = begin_run(g, p);
+  if (rc) return rc;
+  if (!labels_out && g->n > 0) return CD_EINVAL;
+  rc = run_lpa(g, opts_from(p, 0), rounds_out);
+  if (rc) return rc;
+  if (g->n > 0)
+    CD_CHECK(cudaMemcpyAsync(labels_out, g->C, g->n * sizeof(int32_t),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+  CD_CHECK(cudaStreamSynchronize(g->stream));
+  return CD_OK;
+}
+
+int cd_louvain_local_move(cd_graph* g, const cd_params* p, int32_t* labels_io, int init_given,
+                          int on_device, int64_t* moves_out, int32_t* rounds_out) {
+  int rc = begin_run(g, p);
+  if (rc) return rc;
+  if (!labels_io && g->n > 0) return CD_EINVAL;
+  if ((rc = ensure_run_state(g))) return rc;
+  if (init_given && g->n > 0) {
+    CD_CHECK(cudaMemcpyAsync(g->C, labels_io, g->n * sizeof(int32_t),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    if ((rc = check_labels(g, g->C))) return rc;
+  }
+  rc = run_local_move(g, opts_from(p, 0), init_given, moves_out, rounds_out);
+  if (rc) return rc;
+  if (g->n > 0)
+    CD_CHECK(cudaMemcpyAsync(labels_io, g->C, g->n * sizeof(int32_t),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+  CD_CHECK(cudaStreamSynchronize(g->stream));
+  return CD_OK;
+}
+
+}  // extern "C"
