@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Benchmark: Louvain + LPA on one GB300 per rank, through the C ABI.
+
+One step = the whole hot path on one synthetic graph already resident in HBM:
+ingest (validate, deg_w, vol, degree bins), Label Propagation to convergence
+(Algorithm 1), Louvain to convergence (Algorithm 2 local moving + Algorithm 3
+aggregation per level) and the modularity of the result.
+
+value  = arcs scanned by all LPA and Louvain rounds of the step / step time
+         (GTEPS, device time from CUDA events on the library's stream);
+e2e    = the same through the C ABI with HOST buffers: the CSR is copied from
+         pinned host memory inside the timed region and both label arrays are
+         copied back;
+roofline = the dominant kernel's algorithmic bytes per launch / its average
+         CUDA-event launch time, against the measured HBM copy bandwidth.
+
+Multi-GPU: the path does not shard a single graph here (replicas only): under
+torchrun every rank solves its own copy of the workload; value sums all ranks'
+arcs over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, builder kwargs)
+    "rmat26": "R-MAT scale 26, edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05), deduplicated, "
+              "symmetrised, loops removed, unit weights, ids unpermuted, seed 3",
+    "lfr1m": "LFR-style n = 1,000,000, degree power law 2.5 on [5,1000], community sizes 1.5 on "
+             "[20,5000], mu = 0.3, weights U{1..8}, seed 2",
+    "sbm10k": "planted-partition SBM n = 10,000, 100 blocks, p_in = 0.1, p_out = 0.001, seed 1",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="rmat26")
+    ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-arcs", type=float, default=3e8)
+    ap.add_argument("--json-out", default=None)
+    return ap.parse_args()
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_graph(name: str, scale_override, device: str):
+    import synth
+    if name == "rmat26":
+        scale = scale_override or 26
+        g = synth.rmat(scale, 16, seed=3, device=device)
+        g.name = f"rmat{scale}_ef16"
+        return g, scale
+    if name == "lfr1m":
+        return synth.lfr(1_000_000, seed=2).to(device), None
+    return synth.sbm(10000, 100, "0.1", "0.001", seed=1).to(device), None
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ one step
+
+def run_step(cd, g_dev, params, labels_lpa, labels_lv, host=False, g_host=None):
+    """Upload + LPA + Louvain (+ modularity). Returns (arcs, info, profile)."""
+    if host:
+        h = cd.cd_csr_upload(g_host[0], g_host[1], g_host[2])
+    else:
+        h = cd.cd_csr_upload(g_dev.off, g_dev.cols, g_dev.w)
+    rounds = cd.cd_lpa_run(h, params, labels_lpa)
+    tr_lpa = cd.cd_trace_get(h)
+    prof_lpa = cd.cd_profile_get(h) if params.timing else []
+    levels, q = cd.cd_louvain_run(h, params, labels_lv)
+    tr_lv = cd.cd_trace_get(h)
+    prof_lv = cd.cd_profile_get(h) if params.timing else []
+    cd.cd_graph_free(h)
+    arcs = sum(t["arcs"] for t in tr_lpa) + sum(t["arcs"] for t in tr_lv)
+    info = {"lpa_rounds": rounds, "louvain_levels": levels, "louvain_rounds": len(tr_lv), "q": q,
+            "lpa_arcs": sum(t["arcs"] for t in tr_lpa), "louvain_arcs": sum(t["arcs"] for t in tr_lv),
+            "lpa_scan_ms": sum(t["scan_ms"] for t in tr_lpa),
+            "louvain_scan_ms": sum(t["scan_ms"] for t in tr_lv)}
+    return arcs, info, prof_lpa + prof_lv
+
+
+def merge_profiles(acc: dict, prof: list):
+    for p in prof:
+        a = acc.setdefault(p["name"], {"launches": 0, "total_ms": 0.0, "alg_bytes": 0.0})
+        a["launches"] += p["launches"]
+        a["total_ms"] += p["total_ms"]
+        a["alg_bytes"] += p["alg_bytes"]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """dram bytes per launch of `kernel` from a committed ncu summary, or None
+    if the summary is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(workload, {}).get(kernel)
+    if not e:
+        return None
+    src = os.path.join(ROOT, "paper_2507_06471_gb300", "csrc", "scan.cu")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if e.get("scan_cu_sha") != digest:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+
+def oracle_sample(off, cols, w, target_arcs: float, seed: int = 17):
+    """The oracle's first LPA round and first Louvain local-move round on the
+    same graph, with the initial active set a seeded uniform vertex sample
+    holding about target_arcs arcs. Returns (arcs, seconds, description)."""
+    import numpy as np
+    import oracle
+    n = len(off) - 1
+    nnz = int(off[-1])
+    frac = min(1.0, target_arcs / max(nnz, 1))
+    act = (np.random.default_rng(seed).random(n) < frac).astype(np.uint8)
+    t0 = time.perf_counter()
+    _, tr1 = oracle.lpa(off, cols, w, max_iter=1, active_in=act)
+    _, _, tr2 = oracle.local_move(off, cols, w, max_iter=1, active_in=act)
+    dt = time.perf_counter() - t0
+    arcs = int(tr1.arcs[0] + tr2.arcs[0])
+    desc = (f"oracle (plain C, 1 thread): first LPA round + first Louvain local-move round of the "
+            f"same graph, initial active set = seeded uniform {frac:.1%} vertex sample "
+            f"({int(act.sum())} vertices, {int(tr1.arcs[0])} arcs per round)")
+    return arcs, dt, desc
+
+
+def host_graph(g):
+    import numpy as np
+    off = g.off.cpu().numpy().astype(np.int64)
+    cols = g.cols.cpu().numpy().astype(np.int32)
+    w = None if g.w is None else g.w.cpu().numpy().astype(np.int64)
+    return off, cols, w
+
+
+def run_reference(args, rank, world):
+    """The oracle on the host cores, timed on bounded samples of the workload."""
+    if rank != 0:
+        return
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    g, scale = make_graph(args.workload, args.scale, dev)
+    off, cols, w = host_graph(g)
+    del g
+    samples = []
+    for i in range(args.warmup + args.steps):
+        arcs, dt, desc = oracle_sample(off, cols, w, args.cpu_sample_arcs)
+        if i >= args.warmup:
+            samples.append((arcs, dt))
+    arcs = sum(a for a, _ in samples)
+    secs = sum(t for _, t in samples)
+    value = arcs / secs / 1e9
+    line = {"impl": "reference", "metric": "GTEPS (arcs scanned per second over all rounds)",
+            "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(samples)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": f"{args.workload}" + (f"_scale{scale}" if scale else ""),
+                                            "description": WORKLOADS[args.workload]},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ main
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2507_06471_gb300 as cd
+
+    assert torch.cuda.is_available(), "the benchmark needs a CUDA GPU"
+    cd.lib()
+    g, scale = make_graph(args.workload, args.scale, "cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # hand the generator's scratch back before the library allocates
+    n, nnz = g.n, g.nnz
+    labels_lpa = torch.empty(n, dtype=torch.int32, device="cuda")
+    labels_lv = torch.empty(n, dtype=torch.int32, device="cuda")
+    params = cd.cd_params_default()
+    stream = torch.cuda.current_stream()
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        run_step(cd, g, params, labels_lpa, labels_lv)
+    torch.cuda.synchronize()
+
+    # timed region: device-resident inputs, per-kernel CUDA events on
+    params.timing = 1
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = cd.cd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    total_arcs = 0
+    infos = []
+    prof = {}
+    for _ in range(args.steps):
+        arcs, info, p = run_step(cd, g, params, labels_lpa, labels_lv)
+        total_arcs += arcs
+        infos.append(info)
+        merge_profiles(prof, p)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = cd.cd_launch_count() - launches0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms_max = allreduce_max(ms, world)
+    arcs_all = allreduce_sum(float(total_arcs), world)
+    value = arcs_all / (ms_max / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers (pinned)
+    off_h = g.off.cpu().pin_memory()
+    cols_h = g.cols.cpu().pin_memory()
+    w_h = None if g.w is None else g.w.cpu().pin_memory()
+    lab_h1 = torch.empty(n, dtype=torch.int32).pin_memory()
+    lab_h2 = torch.empty(n, dtype=torch.int32).pin_memory()
+    params_e2e = cd.cd_params_default()
+    run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_arcs = 0
+    for _ in range(args.e2e_steps):
+        a, _, _ = run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
+        e2e_arcs += a
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    e2e_value = allreduce_sum(float(e2e_arcs), world) / e2e_s / 1e9
+    h2d = off_h.numel() * 8 + cols_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4)
+    d2h = 2 * n * 4
+
+    # roofline of the dominant kernel (by device time in the timed region)
+    peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    dname, d = dom
+    achieved = (d["alg_bytes"] / d["launches"]) / (d["total_ms"] / d["launches"] / 1e3) / 1e9
+    wl_name = f"{args.workload}" + (f"_scale{scale}" if scale else "")
+    traffic = ncu_traffic(dname, wl_name)
+    total_prof_ms = sum(v["total_ms"] for v in prof.values())
+    kernels = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
+                   "share": round(v["total_ms"] / total_prof_ms, 4) if total_prof_ms else 0,
+                   "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1) if v["total_ms"] else 0}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]) if v["launches"]}
+
+    line = {
+        "metric": "GTEPS per iteration (arcs scanned by all LPA + Louvain rounds / step time)",
+        "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": wl_name, "description": WORKLOADS[args.workload], "n": n, "arcs": nnz,
+                   "l2": "inputs larger than L2 (column array %.1f GB)" % (nnz * 4 / 1e9),
+                   "parallelism": f"replicas x{world}", "schedule": "synchronous rounds, SplitMix64 "
+                   "deferral coin, strict-positive gain, smallest-id ties, singleton rule",
+                   "max_iter": params.max_iter, "max_levels": params.max_levels,
+                   "threshold": params.threshold},
+        "time_to_converge_ms": {"lpa_plus_louvain_step": ms_max / args.steps},
+        "step": infos[-1],
+        "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps},
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        off, cols = off_h.numpy(), cols_h.numpy()
+        w = None if w_h is None else w_h.numpy().astype(np.int64)
+        arcs, dt, desc = oracle_sample(off, cols, w, args.cpu_sample_arcs)
+        line["cpu_baseline"] = {"value": arcs / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                                "sample": desc, "seconds": dt}
+    if rank == 0:
+        print(json.dumps(line))
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,9 @@ const char* cd_status_string(int status);
 /* The last CUDA runtime error seen by the library (cudaError_t as int). */
 int cd_last_cuda_error(void);
 
+/* Number of CUDA kernels the library has launched in this process so far. */
+int64_t cd_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,10 +68,10 @@ def lib():
         L.orc_commit.restype = _INT
         L.orc_commit.argtypes = [_U64, _I32, _I32, _I32]
         L.orc_lpa.restype = _I32
-        L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P]
+        L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P, _P]
         L.orc_local_move.restype = _I32
         L.orc_local_move.argtypes = [_I64, _P, _P, _P, _I32, _INT, _INT, _U64, _I32, _INT, _P, _P,
-                                     _P, _P, _P, _P]
+                                     _P, _P, _P, _P, _P]
         L.orc_aggregate.restype = _I64
         L.orc_aggregate.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]
         L.orc_louvain.restype = _I32
@@ -175,23 +175,32 @@ def _trace(r, tm, td, ta, tr):
     return RunTrace(int(r), tm[:r].copy(), td[:r].copy(), ta[:r].copy(), tr[:r].copy())
 
 
+def _active(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
 def lpa(off, cols, w=None, max_iter=100, threshold=0, tie_keep_current=1, use_frontier=1,
-        sched_seed=DEFAULT_SCHED_SEED):
-    """Algorithm 1 with synchronous rounds; returns (labels int32[n], RunTrace)."""
+        sched_seed=DEFAULT_SCHED_SEED, active_in=None):
+    """Algorithm 1 with synchronous rounds; returns (labels int32[n], RunTrace).
+    active_in: optional initial V_active (n bools), default all vertices."""
     off, cols, w = _csr(off, cols, w)
+    active_in = _active(active_in)
     n = len(off) - 1
     labels = np.zeros(n, dtype=np.int32)
     cap = max(max_iter, 1)
     tm, td, ta, tr = (np.zeros(cap, dtype=np.int64) for _ in range(4))
     r = lib().orc_lpa(n, _ptr(off), _ptr(cols), _ptr(w), max_iter, threshold, tie_keep_current,
-                      use_frontier, sched_seed, _ptr(labels), _ptr(tm), _ptr(td), _ptr(ta), _ptr(tr))
+                      use_frontier, sched_seed, _ptr(active_in), _ptr(labels), _ptr(tm), _ptr(td),
+                      _ptr(ta), _ptr(tr))
     return labels, _trace(r, tm, td, ta, tr)
 
 
 def local_move(off, cols, w=None, max_iter=100, singleton_rule=1, use_frontier=1, labels_in=None,
-               sched_seed=DEFAULT_SCHED_SEED, level=0):
-    """Algorithm 2 with synchronous rounds; returns (labels, total moves, RunTrace)."""
+               sched_seed=DEFAULT_SCHED_SEED, level=0, active_in=None):
+    """Algorithm 2 with synchronous rounds; returns (labels, total moves, RunTrace).
+    active_in: optional initial needCheck (n bools), default all vertices."""
     off, cols, w = _csr(off, cols, w)
+    active_in = _active(active_in)
     n = len(off) - 1
     if labels_in is None:
         labels = np.zeros(n, dtype=np.int32)
@@ -203,8 +212,8 @@ def local_move(off, cols, w=None, max_iter=100, singleton_rule=1, use_frontier=1
     tm, td, ta, tr = (np.zeros(cap, dtype=np.int64) for _ in range(4))
     moves = np.zeros(1, dtype=np.int64)
     r = lib().orc_local_move(n, _ptr(off), _ptr(cols), _ptr(w), max_iter, singleton_rule, use_frontier,
-                             sched_seed, level, given, _ptr(labels), _ptr(moves), _ptr(tm), _ptr(td),
-                             _ptr(ta), _ptr(tr))
+                             sched_seed, level, given, _ptr(active_in), _ptr(labels), _ptr(moves),
+                             _ptr(tm), _ptr(td), _ptr(ta), _ptr(tr))
     if r < 0:
         raise ValueError("labels out of range")
     return labels, int(moves[0]), _trace(r, tm, td, ta, tr)

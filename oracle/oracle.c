@@ -283,8 +283,9 @@ static void mark_next(int64_t n, const int64_t* off, const int32_t* cols,
 int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
                 const int64_t* w, int32_t max_iter, int64_t threshold,
                 int tie_keep_current, int use_frontier, uint64_t sched_seed,
-                int32_t* labels_out, int64_t* tr_moved, int64_t* tr_deferred,
-                int64_t* tr_active, int64_t* tr_arcs) {
+                const unsigned char* active_in, int32_t* labels_out,
+                int64_t* tr_moved, int64_t* tr_deferred, int64_t* tr_active,
+                int64_t* tr_arcs) {
   int32_t* C = labels_out;
   int32_t* nxt = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
   unsigned char* active = (unsigned char*)malloc((size_t)n + 1);
@@ -292,7 +293,10 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
   unsigned char* deferred = (unsigned char*)malloc((size_t)n + 1);
   orc_ws* ws = orc_ws_create(n);
   for (int64_t v = 0; v < n; ++v) C[v] = (int32_t)v; /* singleton labels */
-  memset(active, 1, (size_t)n);                       /* V_active = V */
+  if (active_in)
+    memcpy(active, active_in, (size_t)n);             /* a given V_active */
+  else
+    memset(active, 1, (size_t)n);                     /* V_active = V */
   int32_t rounds = 0;
   for (int32_t r = 0; r < max_iter; ++r) {
     int64_t nact = 0, arcs = 0, nmoved = 0, ndef = 0;
@@ -336,7 +340,8 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
 int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
                        const int64_t* w, int32_t max_iter, int singleton_rule,
                        int use_frontier, uint64_t sched_seed, int32_t level,
-                       int init_given, int32_t* labels_io, int64_t* moves_out,
+                       int init_given, const unsigned char* active_in,
+                       int32_t* labels_io, int64_t* moves_out,
                        int64_t* tr_moved, int64_t* tr_deferred,
                        int64_t* tr_active, int64_t* tr_arcs) {
   int32_t* C = labels_io;
@@ -359,7 +364,10 @@ int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
     sigma[C[v]] += degw[v];
     csize[C[v]] += 1;
   }
-  memset(flag, 1, (size_t)n);
+  if (active_in)
+    memcpy(flag, active_in, (size_t)n); /* a given needCheck */
+  else
+    memset(flag, 1, (size_t)n);
   int64_t total = 0;
   int32_t rounds = 0;
   for (int32_t r = 0; r < max_iter; ++r) {
@@ -506,8 +514,8 @@ int32_t orc_louvain(int64_t n, const int64_t* off, const int32_t* cols,
   for (int32_t lvl = 0; lvl < max_levels; ++lvl) {
     int64_t moves = 0;
     int32_t rounds = orc_local_move(gn, goff, gcols, gw, max_iter, singleton_rule,
-                                    use_frontier, sched_seed, lvl, 0, C, &moves,
-                                    NULL, NULL, NULL, NULL);
+                                    use_frontier, sched_seed, lvl, 0, NULL, C,
+                                    &moves, NULL, NULL, NULL, NULL);
     if (tr_rounds) tr_rounds[lvl] = rounds;
     if (tr_moves) tr_moves[lvl] = moves;
     if (tr_nverts) tr_nverts[lvl] = gn;

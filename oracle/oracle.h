@@ -82,6 +82,7 @@ int32_t orc_louvain_decide(int64_t n, const int64_t* off, const int32_t* cols,
 int orc_commit(uint64_t sched_seed, int32_t level, int32_t round, int32_t v);
 
 /* Algorithm 1 (PLP) with synchronous rounds and the deferral coin.
+ * active_in (n bytes, may be NULL = all of V) is the initial V_active.
  * labels_out[n] receives C. Per-round traces (moved, deferred, active
  * vertices, arcs scanned) go to the optional arrays of length max_iter.
  * Stops after a round with moved + deferred <= threshold. Returns the number
@@ -89,18 +90,21 @@ int orc_commit(uint64_t sched_seed, int32_t level, int32_t round, int32_t v);
 int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
                 const int64_t* w, int32_t max_iter, int64_t threshold,
                 int tie_keep_current, int use_frontier, uint64_t sched_seed,
-                int32_t* labels_out, int64_t* tr_moved, int64_t* tr_deferred,
-                int64_t* tr_active, int64_t* tr_arcs);
+                const unsigned char* active_in, int32_t* labels_out,
+                int64_t* tr_moved, int64_t* tr_deferred, int64_t* tr_active,
+                int64_t* tr_arcs);
 
 /* Algorithm 2 (local moving) with synchronous rounds and the deferral coin of
  * level `level`. If init_given is 0 the partition starts as singletons, else
- * from labels_io (values in [0, n)). labels_io[n] receives comID.
+ * from labels_io (values in [0, n)). active_in (n bytes, may be NULL = all)
+ * is the initial needCheck. labels_io[n] receives comID.
  * *moves_out = total moves over all rounds. Stops after a round in which no
  * vertex moved or deferred. Returns the number of rounds (-1: bad labels). */
 int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
                        const int64_t* w, int32_t max_iter, int singleton_rule,
                        int use_frontier, uint64_t sched_seed, int32_t level,
-                       int init_given, int32_t* labels_io, int64_t* moves_out,
+                       int init_given, const unsigned char* active_in,
+                       int32_t* labels_io, int64_t* moves_out,
                        int64_t* tr_moved, int64_t* tr_deferred,
                        int64_t* tr_active, int64_t* tr_arcs);
 

@@ -27,6 +27,7 @@ EXPORTED = [
     "cd_params_default", "cd_csr_upload", "cd_graph_free", "cd_graph_info", "cd_graph_download",
     "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
     "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
+    "cd_launch_count",
 ]
 
 
@@ -82,6 +83,8 @@ def lib():
         L.cd_status_string.restype = ctypes.c_char_p
         L.cd_status_string.argtypes = [ctypes.c_int]
         L.cd_last_cuda_error.argtypes = []
+        L.cd_launch_count.restype = ctypes.c_int64
+        L.cd_launch_count.argtypes = []
         _lib = L
     return _lib
 
@@ -214,6 +217,10 @@ def cd_profile_get(g):
     _check(lib().cd_profile_get(g, buf, 64, ctypes.byref(cnt)), "cd_profile_get")
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "total_ms": buf[i].total_ms,
              "alg_bytes": buf[i].alg_bytes} for i in range(min(cnt.value, 64))]
+
+
+def cd_launch_count() -> int:
+    return int(lib().cd_launch_count())
 
 
 def cd_status_string(status: int) -> str:

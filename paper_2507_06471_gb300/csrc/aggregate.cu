@@ -183,9 +183,9 @@ int renumber(cd_graph* g, const int32_t* labels_dev, int32_t* newid_dev, int64_t
   {
     KTimer t(g, K_RENUMBER, (double)n * (4 + 1 + 1 + 4 + 1));
     CD_CHECK(cudaMemsetAsync(used, 0, n, s));
-    k_mark_used<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(labels_dev, n, used);
+    CD_LAUNCH(k_mark_used<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(labels_dev, n, used));
     rc = exclusive_scan_u8_to_i32(used, newid_dev, n, total, s);
-    if (!rc) k_fix_unused<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(used, n, newid_dev);
+    if (!rc) CD_LAUNCH(k_fix_unused<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(used, n, newid_dev));
   }
   int64_t k = 0;
   if (!rc && cudaMemcpyAsync(&k, total, 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
@@ -228,11 +228,11 @@ int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, 
     KTimer t(g, K_AGG_EMIT, (double)n * (8 + 4 + 4) + (double)m * (4 + 4 + 4 + wbytes + 16));
     const unsigned gr = grid_cap(n * 32 / NT + 1);
     if (g->wkind == W_UNIT)
-      k_agg_emit<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals);
+      CD_LAUNCH(k_agg_emit<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals));
     else if (g->wkind == W_I32)
-      k_agg_emit<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals);
+      CD_LAUNCH(k_agg_emit<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals));
     else
-      k_agg_emit<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals);
+      CD_LAUNCH(k_agg_emit<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, newid_dev, bits, keys, vals));
   }
   uint64_t* sk = keys;
   int64_t* sv = vals;
@@ -260,8 +260,8 @@ int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, 
     if (!rc) {
       cudaMemsetAsync(rowcnt, 0, k * sizeof(unsigned long long), s);
       if (m > 0) {
-        k_agg_heads<<<grid_cap((m + NT - 1) / NT), NT, 0, s>>>(sk, hx, pre, m, bits, ccols, cw, rowcnt);
-        k_agg_tails<<<grid_cap((m + NT - 1) / NT), NT, 0, s>>>(sk, hx, pre, sv, m, cw);
+        CD_LAUNCH(k_agg_heads<<<grid_cap((m + NT - 1) / NT), NT, 0, s>>>(sk, hx, pre, m, bits, ccols, cw, rowcnt));
+        CD_LAUNCH(k_agg_tails<<<grid_cap((m + NT - 1) / NT), NT, 0, s>>>(sk, hx, pre, sv, m, cw));
       }
       // offsets = exclusive scan of the row counts
       rc = exclusive_scan_i64((const int64_t*)rowcnt, coff, k, nseg_dev, s);
@@ -303,15 +303,15 @@ int modularity(cd_graph* g, const int32_t* labels_dev, double* q_out) {
     KTimer t(g, K_MODULARITY, (double)n * (8 + 4 + 4 + 8 + 8 + 8) + (double)g->nnz * (4 + 4 + wbytes));
     cudaMemsetAsync(volc, 0, n * 8, s);
     cudaMemsetAsync(acc, 0, 3 * 8, s);
-    k_mod_vol<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(labels_dev, g->degw, n, volc);
-    k_mod_sq<<<grid_cap((n + NT - 1) / NT, 152 * 4), NT, 0, s>>>(volc, n, acc);
+    CD_LAUNCH(k_mod_vol<<<grid_cap((n + NT - 1) / NT), NT, 0, s>>>(labels_dev, g->degw, n, volc));
+    CD_LAUNCH(k_mod_sq<<<grid_cap((n + NT - 1) / NT, 152 * 4), NT, 0, s>>>(volc, n, acc));
     const unsigned gr = grid_cap(n * 32 / NT + 1);
     if (g->wkind == W_UNIT)
-      k_mod_internal<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc);
+      CD_LAUNCH(k_mod_internal<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc));
     else if (g->wkind == W_I32)
-      k_mod_internal<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc);
+      CD_LAUNCH(k_mod_internal<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc));
     else
-      k_mod_internal<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc);
+      CD_LAUNCH(k_mod_internal<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, n, labels_dev, acc));
   }
   unsigned long long h[3] = {0, 0, 0};
   CD_CHECK(cudaGetLastError());
@@ -406,7 +406,7 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
   const int64_t n0 = g->n;
   int32_t* labels0 = nullptr;
   if ((rc = dev_alloc_t(&labels0, n0, s))) return rc;
-  if (n0 > 0) k_iota<<<grid_cap((n0 + NT - 1) / NT), NT, 0, s>>>(labels0, n0);
+  if (n0 > 0) CD_LAUNCH(k_iota<<<grid_cap((n0 + NT - 1) / NT), NT, 0, s>>>(labels0, n0));
   cd_graph* cur = g;
   int32_t levels = 0;
   int32_t* newid = nullptr;
@@ -416,7 +416,7 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
     int64_t k = 0;
     if ((rc = dev_alloc_t(&newid, cur->n, s))) break;
     if ((rc = renumber(cur, cur->C, newid, &k))) break;
-    if (n0 > 0) k_compose<<<grid_cap((n0 + NT - 1) / NT), NT, 0, s>>>(labels0, n0, cur->C, newid);
+    if (n0 > 0) CD_LAUNCH(k_compose<<<grid_cap((n0 + NT - 1) / NT), NT, 0, s>>>(labels0, n0, cur->C, newid));
     levels = lvl + 1;
     if (k == cur->n) break;  // done: every vertex is its own community
     cd_graph* coarse = nullptr;

@@ -110,6 +110,11 @@ struct cd_graph {
 
 namespace cd {
 
+// Every kernel launch of the library goes through CD_LAUNCH, which counts it
+// (process-wide; read with cd_launch_count).
+void note_launch();
+#define CD_LAUNCH(...) (::cd::note_launch(), __VA_ARGS__)
+
 // error plumbing
 int set_cuda_error(cudaError_t e);
 #define CD_CHECK(call)                                  \

@@ -6,6 +6,7 @@
 // the plain row sum and aggregation/modularity sum arc weights without special
 // cases. Upload doubles loop arcs; cd_graph_download halves them back.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 
@@ -19,6 +20,9 @@ const char* const kKernelNames[K_COUNT] = {
     "renumber",    "agg_emit",   "radix_sort", "agg_reduce",  "modularity"};
 
 static thread_local int g_last_cuda = 0;
+static std::atomic<long long> g_launches{0};
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int set_cuda_error(cudaError_t e) {
   g_last_cuda = (int)e;
@@ -295,7 +299,7 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
   if ((rc = dev_alloc_t(&d_cur, NBINS, s))) return rc;
   CD_CHECK(cudaMemcpyAsync(d_base, g->bin_start, NBINS * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CD_CHECK(cudaMemsetAsync(d_cur, 0, NBINS * sizeof(unsigned long long), s));
-  if (g->n > 0) k_bin_fill<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, d_base, d_cur, g->bin_list);
+  if (g->n > 0) CD_LAUNCH(k_bin_fill<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, d_base, d_cur, g->bin_list));
   CD_CHECK(cudaGetLastError());
   // hubs: host-side layout of tables and work items
   int64_t nh = g->bin_start[B_HUB + 1] - g->bin_start[B_HUB];
@@ -303,8 +307,8 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
   if (nh > 0) {
     int64_t* d_rows = nullptr;
     if ((rc = dev_alloc_t(&d_rows, 2 * nh, s))) return rc;
-    k_gather_rows<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, g->bin_list + g->bin_start[B_HUB],
-                                                              nh, d_rows);
+    CD_LAUNCH(k_gather_rows<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, g->bin_list + g->bin_start[B_HUB],
+                                                              nh, d_rows));
     std::vector<int64_t> rows(2 * nh);
     CD_CHECK(cudaMemcpyAsync(rows.data(), d_rows, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CD_CHECK(cudaStreamSynchronize(s));
@@ -371,14 +375,14 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
     if (g->n > 0) {
       unsigned gr = grid_for(g->n * 32);
       if (g->wkind == W_UNIT)
-        k_ingest<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                         g->status);
+        CD_LAUNCH(k_ingest<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                         g->status));
       else if (g->wkind == W_I32)
-        k_ingest<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                        g->status);
+        CD_LAUNCH(k_ingest<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                        g->status));
       else
-        k_ingest<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                        g->status);
+        CD_LAUNCH(k_ingest<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
+                                        g->status));
     }
   }
   CD_CHECK(cudaGetLastError());
@@ -409,7 +413,7 @@ int ensure_run_state(cd_graph* g) {
 
 int check_labels(cd_graph* g, const int32_t* labels_dev) {
   if (g->n == 0) return CD_OK;
-  k_labels_check<<<grid_for(g->n), NT, 0, g->stream>>>(labels_dev, g->n, g->status);
+  CD_LAUNCH(k_labels_check<<<grid_for(g->n), NT, 0, g->stream>>>(labels_dev, g->n, g->status));
   CD_CHECK(cudaGetLastError());
   int st = read_status(g);
   return st ? st : CD_OK;
@@ -474,6 +478,8 @@ int cd_params_default(cd_params* p) {
 
 int cd_last_cuda_error(void) { return g_last_cuda; }
 
+int64_t cd_launch_count(void) { return (int64_t)g_launches.load(); }
+
 const char* cd_status_string(int st) {
   switch (st) {
     case CD_OK: return "ok";
@@ -530,11 +536,11 @@ int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols, 
     return e;
   }
   if (offsets_is_i64)
-    k_offsets_check<int64_t><<<grid_for(n + 1), NT, 0, s>>>((const int64_t*)d_off_in, n, nnz, d_off,
-                                                            tmp.status);
+    CD_LAUNCH(k_offsets_check<int64_t><<<grid_for(n + 1), NT, 0, s>>>((const int64_t*)d_off_in, n, nnz, d_off,
+                                                            tmp.status));
   else
-    k_offsets_check<int32_t><<<grid_for(n + 1), NT, 0, s>>>((const int32_t*)d_off_in, n, nnz, d_off,
-                                                            tmp.status);
+    CD_LAUNCH(k_offsets_check<int32_t><<<grid_for(n + 1), NT, 0, s>>>((const int32_t*)d_off_in, n, nnz, d_off,
+                                                            tmp.status));
   int32_t st = 0;
   if (cudaGetLastError() != cudaSuccess ||
       cudaMemcpyAsync(&st, tmp.status, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -582,9 +588,9 @@ int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols, 
       return rc;
     }
     if (d_w)
-      k_double_loops<WI32><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, d_w, n, w64);
+      CD_LAUNCH(k_double_loops<WI32><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, d_w, n, w64));
     else
-      k_double_loops<WUnit><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, nullptr, n, w64);
+      CD_LAUNCH(k_double_loops<WUnit><<<grid_for(n * 32), NT, 0, s>>>(d_off, d_cols, nullptr, n, w64));
     dev_free(d_w, s);
     wint = w64;
     wk = W_I64;
@@ -622,7 +628,7 @@ int cd_graph_download(const cd_graph* g, int64_t* off, int32_t* cols, int64_t* w
     int64_t* tmp = nullptr;
     int rc = dev_alloc_t(&tmp, g->nnz, s);
     if (rc) return rc;
-    k_download_w<<<grid_for(g->n * 32), NT, 0, s>>>(g->off, g->cols, g->w, g->wkind, g->n, tmp);
+    CD_LAUNCH(k_download_w<<<grid_for(g->n * 32), NT, 0, s>>>(g->off, g->cols, g->w, g->wkind, g->n, tmp));
     CD_CHECK(cudaMemcpyAsync(w, tmp, g->nnz * 8, k, s));
     dev_free(tmp, s);
   }

@@ -118,9 +118,9 @@ int scan_impl(In in, T* out, int64_t n, int64_t* total_dev, cudaStream_t s) {
   T* sums = nullptr;
   int rc = dev_alloc_t(&sums, nb, s);
   if (rc) return rc;
-  k_scan_reduce<T, In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums);
-  k_scan_sums<T><<<1, 1024, 0, s>>>(sums, nb, total_dev);
-  k_scan_down<T, In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums, out);
+  CD_LAUNCH(k_scan_reduce<T, In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums));
+  CD_LAUNCH(k_scan_sums<T><<<1, 1024, 0, s>>>(sums, nb, total_dev));
+  CD_LAUNCH(k_scan_down<T, In><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(in, n, sums, out));
   dev_free(sums, s);
   CD_CHECK(cudaGetLastError());
   return CD_OK;
@@ -225,10 +225,10 @@ int radix_sort_pairs(uint64_t* keys, int64_t* vals, uint64_t* keys_tmp, int64_t*
   uint64_t *ka = keys, *kb = keys_tmp;
   int64_t *va = vals, *vb = vals_tmp;
   for (int shift = 0; shift < bits; shift += 8) {
-    k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ntiles, counts);
+    CD_LAUNCH(k_rs_hist<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, n, shift, ntiles, counts));
     rc = exclusive_scan_i64(counts, counts, 256 * ntiles, nullptr, s);
     if (rc) break;
-    k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, n, shift, ntiles, counts, kb, vb);
+    CD_LAUNCH(k_rs_scatter<<<(unsigned)ntiles, RS_THREADS, 0, s>>>(ka, va, n, shift, ntiles, counts, kb, vb));
     std::swap(ka, kb);
     std::swap(va, vb);
   }

@@ -708,60 +708,60 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
   if (cnt(B_HUB) > 0) {
     {
       KTimer t(g, K_HUB_INSERT);
-      k_hub_insert<W><<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s);
+      CD_LAUNCH(k_hub_insert<W><<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
     {
       KTimer t(g, K_HUB_EVAL);
-      k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s, B_HUB);
+      CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s, B_HUB));
     }
     if (g->timing) mark(B_HUB);
   }
   if (cnt(B_BLOCK) > 0) {
     {
       KTimer t(g, K_SCAN_BLOCK);
-      k_scan_block<LOUV, W><<<grid_cap(cnt(B_BLOCK), 152 * 4), NT_BLOCK, block_smem(), st>>>(
-          s, lst(B_BLOCK), cnt(B_BLOCK), B_BLOCK);
+      CD_LAUNCH(k_scan_block<LOUV, W><<<grid_cap(cnt(B_BLOCK), 152 * 4), NT_BLOCK, block_smem(), st>>>(
+          s, lst(B_BLOCK), cnt(B_BLOCK), B_BLOCK));
     }
     if (g->timing) mark(B_BLOCK);
   }
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP);
-      k_scan_warp<LOUV, W><<<grid_cap((cnt(B_WARP) + NW - 1) / NW), NT, warp_smem(), st>>>(
-          s, lst(B_WARP), cnt(B_WARP), B_WARP);
+      CD_LAUNCH(k_scan_warp<LOUV, W><<<grid_cap((cnt(B_WARP) + NW - 1) / NW), NT, warp_smem(), st>>>(
+          s, lst(B_WARP), cnt(B_WARP), B_WARP));
     }
     if (g->timing) mark(B_WARP);
   }
   if (cnt(B_T32) > 0) {
     {
       KTimer t(g, K_SCAN_T32);
-      k_scan_tile<32, LOUV, W><<<grid_cap((cnt(B_T32) + NW - 1) / NW), NT, 0, st>>>(
-          s, lst(B_T32), cnt(B_T32), B_T32);
+      CD_LAUNCH(k_scan_tile<32, LOUV, W><<<grid_cap((cnt(B_T32) + NW - 1) / NW), NT, 0, st>>>(
+          s, lst(B_T32), cnt(B_T32), B_T32));
     }
     if (g->timing) mark(B_T32);
   }
   if (cnt(B_T16) > 0) {
     {
       KTimer t(g, K_SCAN_T16);
-      k_scan_tile<16, LOUV, W><<<grid_cap((cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
-          s, lst(B_T16), cnt(B_T16), B_T16);
+      CD_LAUNCH(k_scan_tile<16, LOUV, W><<<grid_cap((cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
+          s, lst(B_T16), cnt(B_T16), B_T16));
     }
     if (g->timing) mark(B_T16);
   }
   if (cnt(B_T8) > 0) {
     {
       KTimer t(g, K_SCAN_T8);
-      k_scan_tile<8, LOUV, W><<<grid_cap((cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
-          s, lst(B_T8), cnt(B_T8), B_T8);
+      CD_LAUNCH(k_scan_tile<8, LOUV, W><<<grid_cap((cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
+          s, lst(B_T8), cnt(B_T8), B_T8));
     }
     if (g->timing) mark(B_T8);
   }
   if (cnt(B_T4) > 0) {
     {
       KTimer t(g, K_SCAN_T4);
-      k_scan_tile<4, LOUV, W><<<grid_cap((cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
-          s, lst(B_T4), cnt(B_T4), B_T4);
+      CD_LAUNCH(k_scan_tile<4, LOUV, W><<<grid_cap((cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
+          s, lst(B_T4), cnt(B_T4), B_T4));
     }
     if (g->timing) mark(B_T4);
   }
@@ -865,13 +865,13 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
       const unsigned gr = grid_cap((moves + NW - 1) / NW);
       if (louv)
-        k_apply<true><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
-                                         g->sigma, g->csize, fnxt, s.mark);
+        CD_LAUNCH(k_apply<true><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
+                                         g->sigma, g->csize, fnxt, s.mark));
       else
-        k_apply<false><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
-                                          g->sigma, g->csize, fnxt, s.mark);
+        CD_LAUNCH(k_apply<false><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
+                                          g->sigma, g->csize, fnxt, s.mark));
       if (hub_moved && s.mark)
-        k_hub_mark<<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s);
+        CD_LAUNCH(k_hub_mark<<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s));
       CD_CHECK(cudaGetLastError());
     }
     cd_round_trace tr;
@@ -914,8 +914,8 @@ int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out) {
   int rc = ensure_run_state(g);
   if (rc) return rc;
   if (g->n > 0)
-    k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, g->stream>>>(g->C, g->sigma, g->csize,
-                                                                            g->degw, g->n, 0);
+    CD_LAUNCH(k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, g->stream>>>(g->C, g->sigma, g->csize,
+                                                                            g->degw, g->n, 0));
   CD_CHECK(cudaGetLastError());
   return run_rounds(g, o, false, nullptr, rounds_out);
 }
@@ -927,13 +927,13 @@ int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves
   cudaStream_t st = g->stream;
   if (g->n > 0) {
     if (!init_given) {
-      k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize,
-                                                                       g->degw, g->n, 1);
+      CD_LAUNCH(k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize,
+                                                                       g->degw, g->n, 1));
     } else {
       CD_CHECK(cudaMemsetAsync(g->sigma, 0, g->n * sizeof(int64_t), st));
       CD_CHECK(cudaMemsetAsync(g->csize, 0, g->n * sizeof(int32_t), st));
-      k_init_given<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize, g->degw,
-                                                                  g->n);
+      CD_LAUNCH(k_init_given<<<grid_cap((g->n + NT - 1) / NT), NT, 0, st>>>(g->C, g->sigma, g->csize, g->degw,
+                                                                  g->n));
     }
   }
   CD_CHECK(cudaGetLastError());

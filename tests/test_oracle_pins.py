@@ -416,3 +416,23 @@ def test_planted_partition_sanity():
     assert q >= 0.95 * q_planted
     lab_lpa, tr = oracle.lpa(off, cols, w)
     assert tr.moved[-1] + tr.deferred[-1] == 0  # LPA reaches a fixed point
+
+
+def test_initial_active_set():
+    # Algorithm 1 line 5 / Algorithm 2 line 7 with a given initial active set:
+    # all-ones equals the default; vertices outside the set keep their label
+    # in round 1, and the arcs scanned are the set's degrees.
+    g = synth.sbm(3000, 30, "0.1", "0.004", seed=4, wmax=3)
+    off, cols, w = g.numpy()
+    ones = np.ones(g.n, dtype=np.uint8)
+    a, ta = oracle.lpa(off, cols, w)
+    b, tb_ = oracle.lpa(off, cols, w, active_in=ones)
+    assert np.array_equal(a, b) and ta.rounds == tb_.rounds
+    sub = (np.random.default_rng(1).random(g.n) < 0.2).astype(np.uint8)
+    deg = np.diff(off)
+    for fn in (lambda: oracle.lpa(off, cols, w, max_iter=1, active_in=sub)[::1],
+               lambda: oracle.local_move(off, cols, w, max_iter=1, active_in=sub)[::2]):
+        lab, tr = fn()
+        assert np.all(lab[sub == 0] == np.arange(g.n)[sub == 0])
+        assert tr.active[0] == sub.sum() and tr.arcs[0] == deg[sub == 1].sum()
+        assert tr.moved[0] == np.count_nonzero(lab != np.arange(g.n))
