@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-arcs", type=float, default=3e8)
+    ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
     return ap.parse_args()
 
