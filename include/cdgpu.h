@@ -165,6 +165,26 @@ int cd_last_cuda_error(void);
 /* Number of CUDA kernels the library has launched in this process so far. */
 int64_t cd_launch_count(void);
 
+/* Modularity without any device allocation. The paper has no counterpart to
+ * this entry point: it serves callers that cannot call cudaMalloc, such as a
+ * process whose device memory is wholly owned and budgeted by another
+ * allocator, where one more driver allocation may fail or is not allowed.
+ * Same result as cd_csr_upload + cd_modularity: Q of `labels` on the graph
+ * (off: n+1 int64, cols: nnz int32, w: nnz int32 or NULL for unit weights, a
+ * loop arc v->v carrying L; labels: n int32 in [0, n)), all DEVICE pointers
+ * owned by the caller; the work runs on `stream` and the call returns after
+ * *q_out is written. Scratch is a static device array inside the library
+ * (16 MiB, held by every GPU that loads the library until exit), so n may be
+ * at most 2,097,152; larger n gives CD_EINVAL. The first call on each device
+ * looks the array's device address up (with that device current), so make it
+ * before any stream capture. All calls share the array: calls that overlap
+ * on the GPU race and must not be issued. Errors: CD_EINVAL (null pointer, n
+ * too large, label outside [0, n), weight < 1), CD_EBOUNDS (column outside
+ * [0, n)), CD_ENOTSYM (offsets outside [0, nnz] or decreasing), CD_ECUDA. */
+int cd_modularity_noalloc(const int64_t* off, const int32_t* cols, const int32_t* w,
+                          const int32_t* labels, int64_t n, int64_t nnz, void* stream,
+                          double* q_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ EXPORTED = [
     "cd_params_default", "cd_csr_upload", "cd_graph_free", "cd_graph_info", "cd_graph_download",
     "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
     "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
-    "cd_launch_count",
+    "cd_launch_count", "cd_modularity_noalloc",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
         L.cd_last_cuda_error.argtypes = []
         L.cd_launch_count.restype = ctypes.c_int64
         L.cd_launch_count.argtypes = []
+        L.cd_modularity_noalloc.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]
         _lib = L
     return _lib
 
@@ -217,6 +218,21 @@ def cd_profile_get(g):
     _check(lib().cd_profile_get(g, buf, 64, ctypes.byref(cnt)), "cd_profile_get")
     return [{"name": buf[i].name.decode(), "launches": buf[i].launches, "total_ms": buf[i].total_ms,
              "alg_bytes": buf[i].alg_bytes} for i in range(min(cnt.value, 64))]
+
+
+def cd_modularity_noalloc(offsets, cols, w, labels, n: Optional[int] = None, stream=None) -> float:
+    """Modularity without device allocation (device tensors: int64 offsets,
+    int32 cols/w/labels); see cdgpu.h for the size limit and the rules."""
+    n = (len(offsets) - 1) if n is None else n
+    ptrs = [_ptr(x) for x in (offsets, cols, w, labels)]
+    if any(p is not None and not dev for p, dev in ptrs):
+        raise ValueError("cd_modularity_noalloc takes device arrays only")
+    if str(offsets.dtype) != "torch.int64":
+        raise TypeError("offsets must be int64")
+    q = ctypes.c_double()
+    _check(lib().cd_modularity_noalloc(ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0], n, int(len(cols)),
+                                       _stream_ptr(stream), ctypes.byref(q)), "cd_modularity_noalloc")
+    return q.value
 
 
 def cd_launch_count() -> int:
