@@ -419,7 +419,7 @@ def test_planted_partition_sanity():
 
 
 def test_initial_active_set():
-    # Algorithm 1 line 5 / Algorithm 2 line 7 with a given initial active set:
+    # Algorithm 1's V_active / Algorithm 2's needCheck started from a given set:
     # all-ones equals the default; vertices outside the set keep their label
     # in round 1, and the arcs scanned are the set's degrees.
     g = synth.sbm(3000, 30, "0.1", "0.004", seed=4, wmax=3)
