@@ -336,17 +336,19 @@ def main():
     lab_h1 = torch.empty(n, dtype=torch.int32).pin_memory()
     lab_h2 = torch.empty(n, dtype=torch.int32).pin_memory()
     params_e2e = cd.cd_params_default()
-    run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_arcs = 0
-    for _ in range(args.e2e_steps):
-        a, _, _ = run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
-        e2e_arcs += a
-    torch.cuda.synchronize()
-    e2e_s = allreduce_max(time.perf_counter() - t0, world)
-    e2e_value = allreduce_sum(float(e2e_arcs), world) / e2e_s / 1e9
+    e2e_value, e2e_s = None, 0.0
+    if args.e2e_steps > 0:
+        run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_arcs = 0
+        for _ in range(args.e2e_steps):
+            a, _, _ = run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
+            e2e_arcs += a
+        torch.cuda.synchronize()
+        e2e_s = allreduce_max(time.perf_counter() - t0, world)
+        e2e_value = allreduce_sum(float(e2e_arcs), world) / e2e_s / 1e9
     h2d = off_h.numel() * 8 + cols_h.numel() * 4 + (0 if w_h is None else w_h.numel() * 4)
     d2h = 2 * n * 4
 
@@ -377,7 +379,7 @@ def main():
         "time_to_converge_ms": {"lpa_plus_louvain_step": ms_max / args.steps},
         "step": infos[-1],
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / args.e2e_steps},
+                "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / max(1, args.e2e_steps)},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},

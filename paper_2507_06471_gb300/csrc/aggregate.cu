@@ -255,7 +255,8 @@ int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, 
     if (!rc && cudaMemcpyAsync(&nseg, nseg_dev, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) rc = CD_ECUDA;
     if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = CD_ECUDA;
     if (!rc) rc = dev_alloc_t(&coff, k + 1, s);
-    if (!rc) rc = dev_alloc_t(&ccols, nseg, s);
+    if (!rc) rc = dev_alloc_t(&ccols, nseg + COL_PAD, s);
+    if (!rc && cudaMemsetAsync(ccols + nseg, 0, COL_PAD * sizeof(int32_t), s) != cudaSuccess) rc = CD_ECUDA;
     if (!rc) rc = dev_alloc_t(&cw, nseg, s);
     if (!rc) {
       cudaMemsetAsync(rowcnt, 0, k * sizeof(unsigned long long), s);

@@ -16,13 +16,13 @@ constexpr int32_t EMPTY = -1;        // empty hash slot (labels are >= 0)
 constexpr int32_t NOCAND = INT32_MAX;  // "no candidate" community id
 
 // Degree bins of the scan (degree = row length, loops included).
-enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLOCK, B_HUB, NBINS };
-constexpr int WARP_MAX = 256;    // warp per vertex, shared-memory table <= 512 slots
-constexpr int WARP_CAP = 512;
-constexpr int BLOCK_MAX = 4096;  // CTA per vertex, shared-memory table <= 8192 slots
-constexpr int BLOCK_CAP = 8192;
-constexpr int HUB_CHUNK = 16384; // arcs per hub-insert work item
-constexpr int HUB_SLICE = 8192;  // table slots per hub-evaluate work item
+enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_BLK2, B_HUB, NBINS };
+constexpr int WARP_MAX = 256;    // a warp per vertex, table <= 512 slots
+constexpr int BLK1_MAX = 1024;   // 128 threads per vertex, table <= 2048 slots
+constexpr int BLOCK_MAX = 4096;  // 512 threads per vertex, table <= 8192 slots
+constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
+constexpr int HUB_SLICE = 4096;  // histogram entries per hub evaluate item
+constexpr int COL_PAD = 4;       // column arrays carry 4 spare entries for 16-byte loads
 
 // Weight kinds of the device CSR.
 enum WKind { W_UNIT = 0, W_I32 = 1, W_I64 = 2 };
@@ -54,8 +54,8 @@ enum Ctr {
 
 // Per-kernel profiling slots.
 enum Kern {
-  K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLOCK,
-  K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
+  K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLK128,
+  K_SCAN_BLK512, K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
   K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
@@ -75,28 +75,38 @@ struct cd_graph {
   // static degree bins
   int32_t* bin_list = nullptr;           // n vertex ids grouped by bin
   int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
-  // hubs (degree > BLOCK_MAX): global hash tables, work items
-  int64_t nhubs = 0, hub_slots = 0, hub_insert_items = 0, hub_eval_items = 0;
-  int64_t* hub_tab = nullptr;      // nhubs+1 slot offsets (caps are powers of two)
-  int32_t* hub_keys = nullptr;     // hub_slots
-  int64_t* hub_vals = nullptr;     // hub_slots
-  int32_t* hub_ins_hub = nullptr;  // per insert item: hub index
-  int64_t* hub_ins_arc = nullptr;  // per insert item: first arc
-  int32_t* hub_ev_hub = nullptr;   // per evaluate item: hub index
-  int64_t* hub_ev_slot = nullptr;  // per evaluate item: first slot
-  int64_t* hub_ev_first = nullptr; // nhubs+1: first evaluate item of each hub
-  int64_t* hub_part = nullptr;     // per evaluate item: 3 words (key hi, key lo, community)
-  int64_t* hub_cur = nullptr;      // nhubs: weight into the hub's own label
-  int32_t* hub_hascur = nullptr;   // nhubs
-  int32_t* hub_done = nullptr;     // nhubs
+  // hubs (degree > BLOCK_MAX): one persistent label histogram per hub, kept in
+  // step with the labels by the moves of its neighbours. Per hub h, capacity
+  // cap_h = 2 deg + 64 in [hub_tab[h], hub_tab[h+1]): hash slots packing
+  // (label << 32 | entry), and dense entries (label, weight).
+  int64_t nhubs = 0, hub_slots = 0, hub_items = 0, hub_eval_items = 0;
+  int32_t* hub_idx = nullptr;              // n: hub index of a vertex, -1 otherwise
+  int64_t* hub_tab = nullptr;              // nhubs+1
+  unsigned long long* hub_slot = nullptr;  // hub_slots
+  int32_t* hub_ent_label = nullptr;        // hub_slots (-1: unused entry)
+  int64_t* hub_ent_w = nullptr;            // hub_slots
+  int32_t* hub_ent_n = nullptr;            // nhubs: entries handed out
+  int32_t* hub_item_hub = nullptr;         // per build/mark item (HUB_CHUNK arcs): hub
+  int64_t* hub_item_arc = nullptr;         // per build/mark item: first arc
+  int32_t* hub_ev_hub = nullptr;           // per evaluate item (HUB_SLICE entries): hub
+  int32_t* hub_ev_ent = nullptr;           // per evaluate item: first entry
+  int64_t* hub_ev_first = nullptr;         // nhubs+1: first evaluate item of each hub
+  int64_t* hub_part = nullptr;             // per evaluate item: (key hi, key lo, community)
+  int64_t* hub_cur = nullptr;              // nhubs: weight into the hub's own label
+  int32_t* hub_hascur = nullptr;           // nhubs
+  int32_t* hub_done = nullptr;             // nhubs: finished evaluate items this round
+  int32_t* hub_mv = nullptr;               // 3 x nhubs: moved flag, old label, new label
+  int32_t* hub_build = nullptr;            // 1: tables must be rebuilt before the next scan
+  int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
 
   // run state (allocated on first use)
   int32_t* C = nullptr;
   int64_t* sigma = nullptr;
   int32_t* csize = nullptr;
   uint8_t* flag[2] = {nullptr, nullptr};
-  int32_t* mv_v = nullptr;
+  int32_t* mv_v = nullptr;  // committed moves: vertex, new label, old label
   int32_t* mv_c = nullptr;
+  int32_t* mv_a = nullptr;
   int64_t* ctr = nullptr;      // device counters
   int64_t* h_ctr = nullptr;    // pinned host copy
   int32_t* status = nullptr;   // device status word (0 = ok)

@@ -15,9 +15,9 @@
 namespace cd {
 
 const char* const kKernelNames[K_COUNT] = {
-    "ingest",      "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32",
-    "scan_warp",   "scan_block", "hub_insert", "hub_eval",    "apply_moves",
-    "renumber",    "agg_emit",   "radix_sort", "agg_reduce",  "modularity"};
+    "ingest",      "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
+    "scan_blk128", "scan_blk512", "hub_insert", "hub_eval",   "apply_moves", "renumber",
+    "agg_emit",    "radix_sort",  "agg_reduce", "modularity"};
 
 static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};
@@ -102,6 +102,7 @@ int profile_flush(cd_graph* g) {
 namespace {
 
 constexpr int NT = 256;
+constexpr int NSTATS = 4 + NBINS;
 
 __device__ __forceinline__ void fail(int32_t* status, int code) { atomicCAS(status, 0, code); }
 
@@ -111,7 +112,8 @@ __device__ __forceinline__ int bin_of(int64_t d) {
   if (d <= 16) return B_T16;
   if (d <= 32) return B_T32;
   if (d <= WARP_MAX) return B_WARP;
-  if (d <= BLOCK_MAX) return B_BLOCK;
+  if (d <= BLK1_MAX) return B_BLK1;
+  if (d <= BLOCK_MAX) return B_BLK2;
   return B_HUB;
 }
 
@@ -131,14 +133,14 @@ __global__ void k_offsets_check(const OffT* __restrict__ in, int64_t n, int64_t 
 
 // Warp per vertex: bounds-check columns and weights, deg_w with loops twice,
 // loop count, vol(V), per-bin vertex counts. stats: [0] vol, [1] loops,
-// [2] isolated, [3..3+NBINS) bin counts.
+// [2] isolated, [3] largest deg_w, [4..4+NBINS) bin counts.
 template <class W>
 __global__ void __launch_bounds__(NT) k_ingest(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ cols, const void* w,
                                                int64_t n, int loops_twice, int64_t* __restrict__ degw,
                                                unsigned long long* stats, int32_t* status) {
-  __shared__ unsigned long long sb[NBINS + 3];
-  if (threadIdx.x < NBINS + 3) sb[threadIdx.x] = 0;
+  __shared__ unsigned long long sb[NSTATS];
+  if (threadIdx.x < NSTATS) sb[threadIdx.x] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -168,10 +170,11 @@ __global__ void __launch_bounds__(NT) k_ingest(const int64_t* __restrict__ off,
       my_vol += (unsigned long long)s;
       my_loops += (unsigned long long)loops;
       int64_t d = end - beg;
+      atomicMax(&sb[3], (unsigned long long)s);
       if (d == 0)
         atomicAdd(&sb[2], 1ull);
       else
-        atomicAdd(&sb[3 + bin_of(d)], 1ull);
+        atomicAdd(&sb[4 + bin_of(d)], 1ull);
     }
   }
   if (lane == 0) {
@@ -179,7 +182,12 @@ __global__ void __launch_bounds__(NT) k_ingest(const int64_t* __restrict__ off,
     atomicAdd(&sb[1], my_loops);
   }
   __syncthreads();
-  if (threadIdx.x < NBINS + 3 && sb[threadIdx.x]) atomicAdd(&stats[threadIdx.x], sb[threadIdx.x]);
+  if (threadIdx.x < NSTATS && sb[threadIdx.x]) {
+    if (threadIdx.x == 3)
+      atomicMax(&stats[3], sb[3]);
+    else
+      atomicAdd(&stats[threadIdx.x], sb[threadIdx.x]);
+  }
 }
 
 // Internal weights with loop arcs doubled (int64).
@@ -223,6 +231,11 @@ __global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off
       if (b == bb) list[bin_base[bb] + (int64_t)pos + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
     }
   }
+}
+
+__global__ void k_hub_index(const int32_t* __restrict__ hubs, int64_t nh, int32_t* hub_idx) {
+  int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (h < nh) hub_idx[hubs[h]] = (int32_t)h;
 }
 
 __global__ void k_gather_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ vs,
@@ -271,12 +284,13 @@ int read_status(cd_graph* g) {
 
 void free_arrays(cd_graph* g) {
   cudaStream_t s = g->stream;
-  void* ps[] = {g->off,         g->cols,       g->w,           g->degw,        g->bin_list,
-                g->hub_tab,     g->hub_keys,   g->hub_vals,    g->hub_ins_hub, g->hub_ins_arc,
-                g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first, g->hub_part,  g->hub_cur,
-                g->hub_hascur,  g->hub_done,   g->C,           g->sigma,       g->csize,
-                g->flag[0],     g->flag[1],    g->mv_v,        g->mv_c,        g->ctr,
-                g->status};
+  void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
+                g->hub_idx,      g->hub_tab,       g->hub_slot,     g->hub_ent_label, g->hub_ent_w,
+                g->hub_ent_n,    g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_ent,
+                g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
+                g->hub_mv,       g->hub_build,     g->C,            g->sigma,        g->csize,
+                g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
+                g->ctr,          g->status};
   for (void* p : ps) dev_free(p, s);
   if (g->h_ctr) cudaFreeHost(g->h_ctr);
 }
@@ -287,9 +301,10 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
   cudaStream_t s = g->stream;
   g->vol = (int64_t)stats[0];
   g->n_isolated = (int64_t)stats[2];
+  g->max_degw = (int64_t)stats[3];
   if (stats[0] >= (1ull << 62)) return CD_EOVERFLOW;
   g->bin_start[0] = 0;
-  for (int b = 0; b < NBINS; ++b) g->bin_start[b + 1] = g->bin_start[b] + (int64_t)stats[3 + b];
+  for (int b = 0; b < NBINS; ++b) g->bin_start[b + 1] = g->bin_start[b] + (int64_t)stats[4 + b];
   int64_t listed = g->bin_start[NBINS];
   int rc = dev_alloc_t(&g->bin_list, listed, s);
   if (rc) return rc;
@@ -313,49 +328,55 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
     CD_CHECK(cudaMemcpyAsync(rows.data(), d_rows, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CD_CHECK(cudaStreamSynchronize(s));
     dev_free(d_rows, s);
-    std::vector<int64_t> tab(nh + 1, 0), ev_first(nh + 1, 0), ins_arc, ev_slot;
-    std::vector<int32_t> ins_hub, ev_hub;
+    std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0);
+    std::vector<int32_t> item_hub, ev_hub, ev_ent;
     for (int64_t h = 0; h < nh; ++h) {
       int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
-      int64_t cap = deg + deg / 2 + 1;  // load factor <= 2/3 even if every label differs
+      int64_t cap = 2 * deg + 64;  // live labels <= deg; the rest absorbs labels that come and go
       tab[h + 1] = tab[h] + cap;
       for (int64_t a = 0; a < deg; a += HUB_CHUNK) {
-        ins_hub.push_back((int32_t)h);
-        ins_arc.push_back(beg + a);
+        item_hub.push_back((int32_t)h);
+        item_arc.push_back(beg + a);
       }
       ev_first[h] = (int64_t)ev_hub.size();
-      for (int64_t sl = 0; sl < cap; sl += HUB_SLICE) {
+      for (int64_t e = 0; e < cap; e += HUB_SLICE) {
         ev_hub.push_back((int32_t)h);
-        ev_slot.push_back(sl);
+        ev_ent.push_back((int32_t)e);
       }
     }
     ev_first[nh] = (int64_t)ev_hub.size();
     g->hub_slots = tab[nh];
-    g->hub_insert_items = (int64_t)ins_hub.size();
+    g->hub_items = (int64_t)item_hub.size();
     g->hub_eval_items = (int64_t)ev_hub.size();
+    if ((rc = dev_alloc_t(&g->hub_idx, g->n, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_keys, g->hub_slots, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_vals, g->hub_slots, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ins_hub, g->hub_insert_items, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ins_arc, g->hub_insert_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_slot, g->hub_slots, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ent_label, g->hub_slots, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ent_w, g->hub_slots, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ent_n, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_item_hub, g->hub_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_item_arc, g->hub_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_ev_hub, g->hub_eval_items, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ev_slot, g->hub_eval_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ev_ent, g->hub_eval_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_ev_first, nh + 1, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_part, 3 * g->hub_eval_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_cur, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_hascur, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_done, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_mv, 3 * nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_build, 1, s))) return rc;
     CD_CHECK(cudaMemcpyAsync(g->hub_tab, tab.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
-    CD_CHECK(cudaMemcpyAsync(g->hub_ins_hub, ins_hub.data(), ins_hub.size() * 4, cudaMemcpyHostToDevice, s));
-    CD_CHECK(cudaMemcpyAsync(g->hub_ins_arc, ins_arc.data(), ins_arc.size() * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_item_hub, item_hub.data(), item_hub.size() * 4, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_item_arc, item_arc.data(), item_arc.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_hub, ev_hub.data(), ev_hub.size() * 4, cudaMemcpyHostToDevice, s));
-    CD_CHECK(cudaMemcpyAsync(g->hub_ev_slot, ev_slot.data(), ev_slot.size() * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ev_ent, ev_ent.data(), ev_ent.size() * 4, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_first, ev_first.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
-    CD_CHECK(cudaMemsetAsync(g->hub_keys, 0xff, g->hub_slots * 4, s));
-    CD_CHECK(cudaMemsetAsync(g->hub_vals, 0, g->hub_slots * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_idx, 0xff, g->n * 4, s));
+    CD_LAUNCH(k_hub_index<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
+                                                                       g->hub_idx));
     CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
   }
   dev_free(d_base, s);
@@ -366,9 +387,9 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
 int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
   cudaStream_t s = g->stream;
   unsigned long long* d_stats = nullptr;
-  int rc = dev_alloc_t(&d_stats, NBINS + 3, s);
+  int rc = dev_alloc_t(&d_stats, NSTATS, s);
   if (rc) return rc;
-  CD_CHECK(cudaMemsetAsync(d_stats, 0, (NBINS + 3) * sizeof(unsigned long long), s));
+  CD_CHECK(cudaMemsetAsync(d_stats, 0, (NSTATS) * sizeof(unsigned long long), s));
   {
     KTimer t(g, K_UPLOAD, (double)g->nnz * (4 + (g->wkind == W_I32 ? 4 : g->wkind == W_I64 ? 8 : 0)) +
                               (double)g->n * 16);
@@ -386,7 +407,7 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
     }
   }
   CD_CHECK(cudaGetLastError());
-  CD_CHECK(cudaMemcpyAsync(stats_host, d_stats, (NBINS + 3) * sizeof(unsigned long long),
+  CD_CHECK(cudaMemcpyAsync(stats_host, d_stats, (NSTATS) * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));
   dev_free(d_stats, s);
   CD_CHECK(cudaStreamSynchronize(s));
@@ -406,6 +427,7 @@ int ensure_run_state(cd_graph* g) {
   if ((rc = dev_alloc_t(&g->flag[1], g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->mv_v, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->mv_c, g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->mv_a, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->ctr, C_COUNT, s))) return rc;
   if (!g->h_ctr) CD_CHECK(cudaMallocHost(&g->h_ctr, C_COUNT * sizeof(int64_t)));
   return CD_OK;
@@ -436,7 +458,7 @@ int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* c
   profile_reset(g);
   int rc = dev_alloc_t(&g->status, 1, s);
   if (!rc && cudaMemsetAsync(g->status, 0, 4, s) != cudaSuccess) rc = CD_ECUDA;
-  unsigned long long stats[NBINS + 3] = {};
+  unsigned long long stats[NSTATS] = {};
   if (stats_pre) {
     memcpy(stats, stats_pre, sizeof(stats));
   } else {
@@ -512,7 +534,8 @@ int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols, 
   int32_t* d_w = nullptr;
   void* d_off_in = nullptr;
   if (!rc) rc = dev_alloc_t(&d_off, n + 1, s);
-  if (!rc) rc = dev_alloc_t(&d_cols, nnz, s);
+  if (!rc) rc = dev_alloc_t(&d_cols, nnz + COL_PAD, s);
+  if (!rc && cudaMemsetAsync(d_cols + nnz, 0, COL_PAD * sizeof(int32_t), s) != cudaSuccess) rc = CD_ECUDA;
   if (!rc && w) rc = dev_alloc_t(&d_w, nnz, s);
   size_t ob = (size_t)(n + 1) * (offsets_is_i64 ? 8 : 4);
   if (!rc) rc = dev_alloc(&d_off_in, ob, s);
@@ -560,7 +583,7 @@ int cd_csr_upload(const void* offsets, int offsets_is_i64, const int32_t* cols, 
   tmp.w = d_w;
   tmp.wkind = d_w ? W_I32 : W_UNIT;
   rc = dev_alloc_t(&tmp.degw, n, s);
-  unsigned long long stats[NBINS + 3] = {};
+  unsigned long long stats[NSTATS] = {};
   if (!rc) rc = ingest(&tmp, 1, stats);
   if (!rc && cudaMemcpyAsync(&st, tmp.status, 4, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
       cudaStreamSynchronize(s) == cudaSuccess && st)

@@ -24,10 +24,11 @@
 namespace cd {
 namespace {
 
-constexpr int NT = 256;          // threads of tile / warp / hub kernels
-constexpr int NT_BLOCK = 512;    // threads of the CTA-per-vertex kernel
+constexpr int NT = 256;  // threads of the tile and hub-evaluate kernels
 constexpr int NW = NT / 32;
-constexpr int NW_BLOCK = NT_BLOCK / 32;
+constexpr int WARP_CAP_SLOTS = 2 * WARP_MAX;   // table slots per warp-bin vertex
+constexpr int BLK1_CAP_SLOTS = 2 * BLK1_MAX;   // per 128-thread group
+constexpr int BLK2_CAP_SLOTS = 2 * BLOCK_MAX;  // per 512-thread CTA
 
 // ------------------------------------------------------------------ coin
 
@@ -96,22 +97,27 @@ struct ScanCtx {
   int32_t* status;
   uint64_t seed;
   int level, round, tie_keep, singleton_rule;
+  int32_t* mv_a;
   // hubs
   const int32_t* hub_list;
+  const int32_t* hub_idx;
   const int64_t* hub_tab;
-  int32_t* hub_keys;
-  int64_t* hub_vals;
-  const int32_t* hub_ins_hub;
-  const int64_t* hub_ins_arc;
+  unsigned long long* hub_slot;
+  int32_t* hub_ent_label;
+  int64_t* hub_ent_w;
+  int32_t* hub_ent_n;
+  const int32_t* hub_item_hub;
+  const int64_t* hub_item_arc;
   const int32_t* hub_ev_hub;
-  const int64_t* hub_ev_slot;
+  const int32_t* hub_ev_ent;
   const int64_t* hub_ev_first;
   int64_t* hub_part;
   int64_t* hub_cur;
   int32_t* hub_hascur;
   int32_t* hub_done;
-  uint8_t* hub_moved;
-  int64_t n_ins_items, n_ev_items;
+  int32_t* hub_mv;
+  int32_t* hub_build;
+  int64_t n_items, nhubs, n_ev_items;
 };
 
 template <bool LOUV>
@@ -150,6 +156,7 @@ __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t c
     unsigned long long pos = atomicAdd(&s.ctr[C_MOVES], 1ull);
     s.mv_v[pos] = v;
     s.mv_c[pos] = target;
+    s.mv_a[pos] = cur;
     return 0;
   }
   return 1;
@@ -255,6 +262,7 @@ __global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __re
         const unsigned long long pos = pos0 + __popc(am & ((1u << lane) - 1u));
         s.mv_v[pos] = v;
         s.mv_c[pos] = target;
+        s.mv_a[pos] = cur;
       }
     }
     if (s.mark) {
@@ -273,272 +281,302 @@ __global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __re
 
 // ------------------------------------------------------------------ shared-memory tables
 
-__device__ __forceinline__ bool smem_insert(int32_t* keys, int64_t* vals, unsigned lg, int32_t key,
-                                            int64_t w, int32_t* status) {
+// Open addressing with linear probing; capacity 2^lg >= 2 x the arcs inserted,
+// so a free slot is always found within `cap` probes.
+template <class V>
+__device__ __forceinline__ void smem_insert(int32_t* keys, V* vals, unsigned lg, int32_t key, V w,
+                                            int32_t* status) {
   const unsigned mask = (1u << lg) - 1u;
   unsigned h = ((uint32_t)key * 2654435761u) >> (32 - lg);
   for (unsigned probe = 0; probe <= mask; ++probe) {
-    int32_t prev = atomicCAS(&keys[h], EMPTY, key);
+    const int32_t prev = atomicCAS(&keys[h], EMPTY, key);
     if (prev == EMPTY || prev == key) {
-      atomicAdd((unsigned long long*)&vals[h], (unsigned long long)w);
-      return true;
+      atomicAdd(vals + h, w);
+      return;
     }
     h = (h + 1) & mask;
   }
-  atomicCAS(status, 0, CD_ETIMEOUT);  // table full: cannot happen with cap >= 2 deg
-  return false;
+  atomicCAS(status, 0, CD_ETIMEOUT);  // table full: impossible with cap >= 2 deg
 }
 
 __device__ __forceinline__ unsigned ceil_log2(int64_t x) {
   unsigned lg = 0;
   while (((int64_t)1 << lg) < x) ++lg;
-  return lg;
+  return lg < 1 ? 1 : lg;
 }
 
-// Warp per vertex, degree 33..WARP_MAX, table of next_pow2(2 deg) slots.
-template <bool LOUV, class W>
-__global__ void __launch_bounds__(NT) k_scan_warp(ScanCtx s, const int32_t* __restrict__ list,
-                                                  int64_t count, int bin) {
+// Synchronise the GROUP threads sharing a table: a warp, the whole CTA, or a
+// named barrier (ids 1..15) for a sub-CTA group.
+template <int GROUP, int NTB>
+__device__ __forceinline__ void group_sync(int gid) {
+  if constexpr (GROUP == 32)
+    __syncwarp();
+  else if constexpr (GROUP == NTB)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "n"(GROUP) : "memory");
+}
+
+// Insert the arcs [beg, end) of vertex v into a group's table. Columns are
+// read 16 bytes at a time (4 arcs per lane, 4 label gathers in flight); equal
+// labels inside a warp are combined with __match_any_sync before the atomics.
+// Column arrays carry COL_PAD spare entries, so a 16-byte load that starts
+// before `end` stays inside the allocation.
+template <class W, class V, int GROUP>
+__device__ __forceinline__ void group_insert(const ScanCtx& s, int32_t v, int64_t beg, int64_t end,
+                                             int gl, int32_t* keys, V* vals, unsigned lg,
+                                             int64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const int wig = gl >> 5;
+  const int64_t a0 = beg & ~(int64_t)3;
+  for (int64_t wb = a0 + (int64_t)wig * 128; wb < end; wb += (int64_t)GROUP * 4) {
+    const int64_t base = wb + 4 * lane;
+    const int4 c4 = base < end ? __ldg(reinterpret_cast<const int4*>(s.cols + base)) : make_int4(0, 0, 0, 0);
+    const int32_t cs[4] = {c4.x, c4.y, c4.z, c4.w};
+    int32_t lbl[4];
+    int64_t wt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t e = base + j;
+      const bool has = e >= beg && e < end;
+      const bool cand = has && cs[j] != v;
+      lbl[j] = cand ? s.C[cs[j]] : (int32_t)(0x80000000u | (unsigned)(lane * 4 + j));
+      wt[j] = (has && !W::unit) ? W::get(s.w, e) : 1;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const unsigned peers = __match_any_sync(FULL, lbl[j]);
+      const int64_t gsum = group_sum<W>(peers, wt[j], stage);
+      if (lbl[j] >= 0 && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl[j], (V)gsum, s.status);
+    }
+  }
+}
+
+// Scan a group's table: take every occupied slot as a candidate, clear it.
+template <bool LOUV, class V, int GROUP>
+__device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_t dv, int gl,
+                                           int32_t* keys, V* vals, int cap,
+                                           typename KeyOf<LOUV>::T& bk, int32_t& bc, bool& hc,
+                                           int64_t& kc, int64_t& ncand) {
+  for (int j = gl; j < cap; j += GROUP) {
+    const int32_t c = keys[j];
+    if (c == EMPTY) continue;
+    const int64_t k = (int64_t)vals[j];
+    keys[j] = EMPTY;
+    vals[j] = 0;
+    ++ncand;
+    if (c == cur) {
+      hc = true;
+      kc = k;
+      if (LOUV) continue;
+    }
+    const typename KeyOf<LOUV>::T key = cand_key<LOUV>(s, c, k, dv);
+    if (better(key, c, bk, bc)) {
+      bk = key;
+      bc = c;
+    }
+  }
+}
+
+// GROUP threads per vertex (a warp, or a named-barrier group of 128 or 512
+// threads), each group with its own CAP-slot shared-memory table.
+template <bool LOUV, class W, class V, int GROUP, int NTB, int CAP, int BIN>
+__global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __restrict__ list,
+                                                    int64_t count) {
   typedef typename KeyOf<LOUV>::T K;
+  constexpr int GPB = NTB / GROUP;  // groups per CTA
+  constexpr int WPG = GROUP / 32;   // warps per group
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ K red_k[GPB][WPG];
+  __shared__ int32_t red_c[GPB][WPG];
+  __shared__ int64_t red_kc[GPB][WPG];
+  __shared__ int32_t red_hc[GPB][WPG];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int64_t* vals = (int64_t*)smem + (size_t)wid * WARP_CAP;
-  int32_t* keys = (int32_t*)(smem + (size_t)NW * WARP_CAP * 8) + (size_t)wid * WARP_CAP;
-  int64_t* stage = (int64_t*)(smem + (size_t)NW * WARP_CAP * 12) + wid * 32;
-  for (int j = lane; j < WARP_CAP; j += 32) {
+  const int gid = threadIdx.x / GROUP, gl = threadIdx.x % GROUP, wig = gl >> 5;
+  V* vals = (V*)smem + (size_t)gid * CAP;
+  int32_t* keys = (int32_t*)(smem + (size_t)GPB * CAP * sizeof(V)) + (size_t)gid * CAP;
+  int64_t* stage = (int64_t*)(smem + (size_t)GPB * CAP * (sizeof(V) + 4)) + wid * 32;
+  for (int j = gl; j < CAP; j += GROUP) {
     keys[j] = EMPTY;
     vals[j] = 0;
   }
-  __syncwarp();
-  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  group_sync<GROUP, NTB>(gid);
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
-  for (int64_t i = warp; i < count; i += nwarps) {
+  for (int64_t i = (int64_t)blockIdx.x * GPB + gid; i < count; i += (int64_t)gridDim.x * GPB) {
     const int32_t v = list[i];
-    if (!is_active(s, v)) continue;  // warp-uniform
+    if (!is_active(s, v)) continue;  // uniform within the group
     const int64_t beg = s.off[v], end = s.off[v + 1];
     const int64_t d = end - beg;
     const unsigned lg = ceil_log2(2 * d);
-    const int cap = 1 << lg;
     const int32_t cur = s.C[v];
-    for (int64_t e0 = beg; e0 < end; e0 += 32) {
-      const int64_t e = e0 + lane;
-      const bool has = e < end;
-      const int32_t u = has ? s.cols[e] : v;
-      const int64_t wt = has ? W::get(s.w, e) : 0;
-      const bool cand = has && u != v;
-      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
-      const unsigned peers = __match_any_sync(FULL, lbl);
-      const int64_t gsum = group_sum<W>(peers, wt, stage);
-      if (cand && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl, gsum, s.status);
-    }
-    __syncwarp();
+    group_insert<W, V, GROUP>(s, v, beg, end, gl, keys, vals, lg, stage);
+    group_sync<GROUP, NTB>(gid);
     const int64_t dv = LOUV ? s.degw[v] : 0;
     K bk = K(0);
     int32_t bc = NOCAND;
     bool hc = false;
     int64_t kc = 0;
-    for (int j = lane; j < cap; j += 32) {
-      const int32_t c = keys[j];
-      if (c == EMPTY) continue;
-      const int64_t k = vals[j];
-      keys[j] = EMPTY;
-      vals[j] = 0;
-      ++n_cand;
-      if (c == cur) {
-        hc = true;
-        kc = k;
+    group_eval<LOUV, V, GROUP>(s, cur, dv, gl, keys, vals, 1 << lg, bk, bc, hc, kc, n_cand);
+    reduce_best(bk, bc, 32);
+    unsigned hm = __ballot_sync(FULL, hc);
+    if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
+    if constexpr (WPG > 1) {
+      if (lane == 0) {
+        red_k[gid][wig] = bk;
+        red_c[gid][wig] = bc;
+        red_hc[gid][wig] = hm != 0;
+        red_kc[gid][wig] = kc;
       }
-      if (LOUV && c == cur) continue;
-      const K key = cand_key<LOUV>(s, c, k, dv);
-      if (better(key, c, bk, bc)) {
-        bk = key;
-        bc = c;
+      group_sync<GROUP, NTB>(gid);
+      if (wig == 0) {
+        bk = lane < WPG ? red_k[gid][lane] : K(0);
+        bc = lane < WPG ? red_c[gid][lane] : NOCAND;
+        reduce_best(bk, bc, 32);
+        hm = __ballot_sync(FULL, lane < WPG && red_hc[gid][lane]);
+        kc = hm ? red_kc[gid][__ffs(hm) - 1] : 0;
       }
     }
-    reduce_best(bk, bc, 32);
-    const unsigned hm = __ballot_sync(FULL, hc);
-    if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
-    __syncwarp();
-    if (lane == 0) {
+    if (gl == 0) {
       const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc);
       n_def += act_single(s, v, cur, target);
       ++n_act;
       n_arcs += d;
     }
+    group_sync<GROUP, NTB>(gid);  // tables and reduction slots are reused
   }
-  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
-}
-
-// CTA per vertex, degree WARP_MAX+1..BLOCK_MAX.
-template <bool LOUV, class W>
-__global__ void __launch_bounds__(NT_BLOCK) k_scan_block(ScanCtx s, const int32_t* __restrict__ list,
-                                                         int64_t count, int bin) {
-  typedef typename KeyOf<LOUV>::T K;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ K red_k[NW_BLOCK];
-  __shared__ int32_t red_c[NW_BLOCK];
-  __shared__ int64_t s_kcur;
-  __shared__ int s_hascur;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int64_t* vals = (int64_t*)smem;
-  int32_t* keys = (int32_t*)(smem + (size_t)BLOCK_CAP * 8);
-  int64_t* stage = (int64_t*)(smem + (size_t)BLOCK_CAP * 12) + wid * 32;
-  for (int j = threadIdx.x; j < BLOCK_CAP; j += NT_BLOCK) {
-    keys[j] = EMPTY;
-    vals[j] = 0;
-  }
-  if (threadIdx.x == 0) {
-    s_hascur = 0;
-    s_kcur = 0;
-  }
-  __syncthreads();
-  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
-  for (int64_t i = blockIdx.x; i < count; i += gridDim.x) {
-    const int32_t v = list[i];
-    if (!is_active(s, v)) continue;  // CTA-uniform
-    const int64_t beg = s.off[v], end = s.off[v + 1];
-    const int64_t d = end - beg;
-    const unsigned lg = ceil_log2(2 * d);
-    const int cap = 1 << lg;
-    const int32_t cur = s.C[v];
-    for (int64_t e0 = beg + wid * 32; e0 < end; e0 += NT_BLOCK) {
-      const int64_t e = e0 + lane;
-      const bool has = e < end;
-      const int32_t u = has ? s.cols[e] : v;
-      const int64_t wt = has ? W::get(s.w, e) : 0;
-      const bool cand = has && u != v;
-      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
-      const unsigned peers = __match_any_sync(FULL, lbl);
-      const int64_t gsum = group_sum<W>(peers, wt, stage);
-      if (cand && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl, gsum, s.status);
-    }
-    __syncthreads();
-    const int64_t dv = LOUV ? s.degw[v] : 0;
-    K bk = K(0);
-    int32_t bc = NOCAND;
-    for (int j = threadIdx.x; j < cap; j += NT_BLOCK) {
-      const int32_t c = keys[j];
-      if (c == EMPTY) continue;
-      const int64_t k = vals[j];
-      keys[j] = EMPTY;
-      vals[j] = 0;
-      ++n_cand;
-      if (c == cur) {
-        s_hascur = 1;
-        s_kcur = k;
-      }
-      if (LOUV && c == cur) continue;
-      const K key = cand_key<LOUV>(s, c, k, dv);
-      if (better(key, c, bk, bc)) {
-        bk = key;
-        bc = c;
-      }
-    }
-    reduce_best(bk, bc, 32);
-    if (lane == 0) {
-      red_k[wid] = bk;
-      red_c[wid] = bc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w2 = 1; w2 < NW_BLOCK; ++w2)
-        if (better(red_k[w2], red_c[w2], bk, bc)) {
-          bk = red_k[w2];
-          bc = red_c[w2];
-        }
-      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, s_hascur != 0, s_kcur);
-      n_def += act_single(s, v, cur, target);
-      ++n_act;
-      n_arcs += d;
-      s_hascur = 0;
-      s_kcur = 0;
-    }
-    __syncthreads();
-  }
-  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def);
 }
 
 // ------------------------------------------------------------------ hubs
+//
+// A hub keeps k_{v,c} for every neighbour label c in a persistent histogram:
+// built from its row when the run (or level) starts, then updated by every
+// committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
+// therefore reads its distinct labels instead of its whole row.
 
-__device__ __forceinline__ void global_insert(int32_t* keys, int64_t* vals, int64_t cap, int32_t key,
-                                              int64_t w, int32_t* status) {
-  int64_t h = (int64_t)(((uint64_t)((uint32_t)key * 2654435761u) * (uint64_t)cap) >> 32);
+constexpr unsigned long long SLOT_EMPTY = ~0ull;
+
+// k_{h,label} += w in hub h's histogram. A label not present takes the next
+// dense entry and publishes (label << 32 | entry) in its hash slot; an entry
+// lost to a concurrent insert of the same label stays unused (label -1). If
+// the entries run out, the rebuild flag is raised.
+__device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
+  const int64_t base = s.hub_tab[h];
+  const int64_t cap = s.hub_tab[h + 1] - base;
+  unsigned long long* slots = s.hub_slot + base;
+  int64_t slot = (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
   for (int64_t probe = 0; probe < cap; ++probe) {
-    int32_t prev = atomicCAS(&keys[h], EMPTY, key);
-    if (prev == EMPTY || prev == key) {
-      atomicAdd((unsigned long long*)&vals[h], (unsigned long long)w);
+    unsigned long long cur = slots[slot];
+    if (cur == SLOT_EMPTY) {
+      const int32_t e = atomicAdd(&s.hub_ent_n[h], 1);
+      if (e >= cap) {
+        atomicExch(s.hub_build, 1);
+        return;
+      }
+      const unsigned long long mine = ((unsigned long long)(uint32_t)label << 32) | (uint32_t)e;
+      cur = atomicCAS(&slots[slot], SLOT_EMPTY, mine);
+      if (cur == SLOT_EMPTY) {
+        s.hub_ent_label[base + e] = label;
+        atomicAdd((unsigned long long*)&s.hub_ent_w[base + e], (unsigned long long)w);
+        return;
+      }
+    }
+    if ((int32_t)(cur >> 32) == label) {
+      atomicAdd((unsigned long long*)&s.hub_ent_w[base + (uint32_t)cur], (unsigned long long)w);
       return;
     }
-    h = h + 1 == cap ? 0 : h + 1;
+    slot = slot + 1 == cap ? 0 : slot + 1;
   }
-  atomicCAS(status, 0, CD_ETIMEOUT);
+  atomicExch(s.hub_build, 1);  // no free slot: rebuild before the next scan
 }
 
-// Every CTA item inserts up to HUB_CHUNK arcs of one hub into its table.
-template <class W>
-__global__ void __launch_bounds__(NT) k_hub_insert(ScanCtx s) {
-  __shared__ int64_t stage[NW][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int64_t it = blockIdx.x; it < s.n_ins_items; it += gridDim.x) {
-    const int32_t h = s.hub_ins_hub[it];
+// Clear every hub histogram when a rebuild is due (flag set).
+__global__ void __launch_bounds__(NT) k_hub_clear(ScanCtx s, int64_t slots) {
+  if (!*(volatile int32_t*)s.hub_build) return;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < slots; i += stride) {
+    s.hub_slot[i] = SLOT_EMPTY;
+    s.hub_ent_label[i] = -1;
+    s.hub_ent_w[i] = 0;
+  }
+  for (int64_t h = (int64_t)blockIdx.x * NT + threadIdx.x; h < s.nhubs; h += stride) s.hub_ent_n[h] = 0;
+}
+
+constexpr int HUB_NT = 512;
+constexpr int HUB_CAP = 2 * HUB_CHUNK;
+static_assert(HUB_CAP == 8192, "hub chunk table");
+
+// Rebuild (flag set): every item is one HUB_CHUNK-arc chunk of a hub row,
+// combined in a shared-memory table, then added to the hub's histogram.
+template <class W, class V>
+__global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
+  if (!*(volatile int32_t*)s.hub_build) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* vals = (V*)smem;
+  int32_t* keys = (int32_t*)(smem + (size_t)HUB_CAP * sizeof(V));
+  int64_t* stage = (int64_t*)(smem + (size_t)HUB_CAP * (sizeof(V) + 4)) + (threadIdx.x >> 5) * 32;
+  for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {
+    keys[j] = EMPTY;
+    vals[j] = 0;
+  }
+  __syncthreads();
+  for (int64_t it = blockIdx.x; it < s.n_items; it += gridDim.x) {
+    const int32_t h = s.hub_item_hub[it];
     const int32_t v = s.hub_list[h];
-    if (!is_active(s, v)) continue;
-    const int64_t a0 = s.hub_ins_arc[it];
+    const int64_t a0 = s.hub_item_arc[it];
     const int64_t rowend = s.off[v + 1];
     const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
-    int32_t* keys = s.hub_keys + s.hub_tab[h];
-    int64_t* vals = s.hub_vals + s.hub_tab[h];
-    const int64_t cap = s.hub_tab[h + 1] - s.hub_tab[h];
-    for (int64_t e0 = a0 + wid * 32; e0 < end; e0 += NT) {
-      const int64_t e = e0 + lane;
-      const bool has = e < end;
-      const int32_t u = has ? s.cols[e] : v;
-      const int64_t wt = has ? W::get(s.w, e) : 0;
-      const bool cand = has && u != v;
-      const int32_t lbl = cand ? s.C[u] : (int32_t)(0x80000000u | (unsigned)lane);
-      const unsigned peers = __match_any_sync(FULL, lbl);
-      const int64_t gsum = group_sum<W>(peers, wt, stage[wid]);
-      if (cand && (__ffs(peers) - 1) == lane) global_insert(keys, vals, cap, lbl, gsum, s.status);
+    group_insert<W, V, HUB_NT>(s, v, a0, end, threadIdx.x, keys, vals, 13, stage);
+    __syncthreads();
+    for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {
+      const int32_t c = keys[j];
+      if (c == EMPTY) continue;
+      const int64_t k = (int64_t)vals[j];
+      keys[j] = EMPTY;
+      vals[j] = 0;
+      hub_hist_add(s, h, c, k);
     }
+    __syncthreads();
   }
 }
 
-// Every CTA item scans HUB_SLICE slots of one hub's table (and clears them);
-// the last item of a hub to finish reduces the partial results and decides.
+// Every item scans HUB_SLICE histogram entries of one active hub; the last
+// item of a hub to finish combines the partial bests and decides. Entries
+// with weight 0 (labels that left the neighbourhood) are not candidates.
 template <bool LOUV>
-__global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s, int bin) {
+__global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   typedef typename KeyOf<LOUV>::T K;
   __shared__ K red_k[NW];
   __shared__ int32_t red_c[NW];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s.hub_build = 0;  // the build (if any) is done
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
   for (int64_t it = blockIdx.x; it < s.n_ev_items; it += gridDim.x) {
     const int32_t h = s.hub_ev_hub[it];
     const int32_t v = s.hub_list[h];
-    if (!is_active(s, v)) continue;
+    if (!is_active(s, v)) continue;  // uniform within the CTA
     const int32_t cur = s.C[v];
     const int64_t dv = LOUV ? s.degw[v] : 0;
-    int32_t* keys = s.hub_keys + s.hub_tab[h];
-    int64_t* vals = s.hub_vals + s.hub_tab[h];
-    const int64_t cap = s.hub_tab[h + 1] - s.hub_tab[h];
-    const int64_t s0 = s.hub_ev_slot[it];
-    const int64_t s1 = s0 + HUB_SLICE < cap ? s0 + HUB_SLICE : cap;
+    const int64_t base = s.hub_tab[h];
+    const int64_t cap = s.hub_tab[h + 1] - base;
+    int64_t cnt = s.hub_ent_n[h];
+    cnt = cnt < cap ? cnt : cap;
+    const int64_t e0 = s.hub_ev_ent[it];
+    const int64_t e1 = e0 + HUB_SLICE < cnt ? e0 + HUB_SLICE : cnt;
     K bk = K(0);
     int32_t bc = NOCAND;
-    for (int64_t j = s0 + threadIdx.x; j < s1; j += NT) {
-      const int32_t c = keys[j];
-      if (c == EMPTY) continue;
-      const int64_t k = vals[j];
-      keys[j] = EMPTY;
-      vals[j] = 0;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) {
+      const int32_t c = s.hub_ent_label[base + e];
+      if (c < 0) continue;
+      const int64_t k = s.hub_ent_w[base + e];
+      if (k == 0) continue;
       ++n_cand;
       if (c == cur) {
         s.hub_cur[h] = k;
         s.hub_hascur[h] = 1;
+        if (LOUV) continue;
       }
-      if (LOUV && c == cur) continue;
       const K key = cand_key<LOUV>(s, c, k, dv);
       if (better(key, c, bk, bc)) {
         bk = key;
@@ -557,24 +595,22 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s, int bin) {
           bk = red_k[w2];
           bc = red_c[w2];
         }
-      i128 kk = (i128)bk;
+      const i128 kk = (i128)bk;
       s.hub_part[3 * it] = (int64_t)(kk >> 64);
       s.hub_part[3 * it + 1] = (int64_t)(uint64_t)kk;
       s.hub_part[3 * it + 2] = bc;
       __threadfence();
-      const int64_t first = s.hub_ev_first[h], nparts = s.hub_ev_first[h + 1] - first;
+      const int64_t nparts = s.hub_ev_first[h + 1] - s.hub_ev_first[h];
       s_last = atomicAdd(&s.hub_done[h], 1) == (int)(nparts - 1);
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
       __threadfence();
-      const int64_t first = s.hub_ev_first[h], last = s.hub_ev_first[h + 1];
       const volatile int64_t* part = s.hub_part;
       K fk = K(0);
       int32_t fc = NOCAND;
-      for (int64_t p = first; p < last; ++p) {
-        const i128 pk = (i128)(((unsigned __int128)(uint64_t)part[3 * p] << 64) |
-                               (uint64_t)part[3 * p + 1]);
+      for (int64_t p = s.hub_ev_first[h]; p < s.hub_ev_first[h + 1]; ++p) {
+        const i128 pk = (i128)(((unsigned __int128)(uint64_t)part[3 * p] << 64) | (uint64_t)part[3 * p + 1]);
         const int32_t pc = (int32_t)part[3 * p + 2];
         if (better((K)pk, pc, fk, fc)) {
           fk = (K)pk;
@@ -586,7 +622,11 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s, int bin) {
       const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc);
       const int def = act_single(s, v, cur, target);
       n_def += def;
-      if (target != cur && !def) s.hub_moved[h] = 1;
+      if (target != cur && !def) {
+        s.hub_mv[3 * h] = 1;
+        s.hub_mv[3 * h + 1] = cur;
+        s.hub_mv[3 * h + 2] = target;
+      }
       ++n_act;
       n_arcs += s.off[v + 1] - s.off[v];
       s.hub_done[h] = 0;
@@ -595,31 +635,26 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s, int bin) {
     }
     __syncthreads();
   }
-  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
 }
 
 // ------------------------------------------------------------------ apply
 
-// Warp per committed move: new label, Sigma_tot and community sizes (Louvain),
-// and the next-round flags of the neighbours of vertices with 33..BLOCK_MAX arcs
-// (tile kernels flag their own; hubs are flagged by k_hub_mark).
-template <bool LOUV>
-__global__ void __launch_bounds__(NT) k_apply(const int32_t* __restrict__ mv_v,
-                                              const int32_t* __restrict__ mv_c, int64_t nmoves,
-                                              const int64_t* __restrict__ off,
-                                              const int32_t* __restrict__ cols,
-                                              const int64_t* __restrict__ degw, int32_t* C,
-                                              int64_t* sigma, int32_t* csize, uint8_t* flag_nxt,
-                                              int mark) {
+// Warp per committed move (vertex v: A -> c): new label, Sigma_tot and
+// community sizes (Louvain); next-round flags of the neighbours of vertices
+// with 33..BLOCK_MAX arcs (tile kernels flag their own, hubs are handled by
+// k_hub_mark); and the histograms of the hubs among v's neighbours.
+template <bool LOUV, class W>
+__global__ void __launch_bounds__(NT) k_apply(ScanCtx s, int64_t nmoves, int64_t* sigma,
+                                              int32_t* csize, int32_t* C) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   for (int64_t m = warp; m < nmoves; m += nwarps) {
-    const int32_t v = mv_v[m], c = mv_c[m];
+    const int32_t v = s.mv_v[m], c = s.mv_c[m], A = s.mv_a[m];
     if (lane == 0) {
       if (LOUV) {
-        const int32_t A = C[v];
-        const int64_t d = degw[v];
+        const int64_t d = s.degw[v];
         atomicAdd((unsigned long long*)&sigma[A], (unsigned long long)(-d));
         atomicAdd((unsigned long long*)&sigma[c], (unsigned long long)d);
         atomicSub(&csize[A], 1);
@@ -627,23 +662,48 @@ __global__ void __launch_bounds__(NT) k_apply(const int32_t* __restrict__ mv_v,
       }
       C[v] = c;
     }
-    if (mark) {
-      const int64_t beg = off[v], end = off[v + 1];
-      if (end - beg > 32 && end - beg <= BLOCK_MAX)
-        for (int64_t e = beg + lane; e < end; e += 32) flag_nxt[cols[e]] = 1;
+    const int64_t beg = s.off[v], end = s.off[v + 1];
+    if (end - beg > BLOCK_MAX) continue;  // a hub: k_hub_mark
+    const bool flag = s.mark && end - beg > 32;
+    if (!flag && s.nhubs == 0) continue;
+    for (int64_t e = beg + lane; e < end; e += 32) {
+      const int32_t u = s.cols[e];
+      if (flag) s.flag_nxt[u] = 1;
+      if (s.nhubs > 0 && u != v) {
+        const int32_t h = s.hub_idx[u];
+        if (h >= 0) {
+          const int64_t w = W::get(s.w, e);
+          hub_hist_add(s, h, A, -w);
+          hub_hist_add(s, h, c, w);
+        }
+      }
     }
   }
 }
 
+// Moved hubs, one item per HUB_CHUNK arcs: flag the neighbours and update the
+// histograms of neighbouring hubs.
+template <class W>
 __global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
-  for (int64_t it = blockIdx.x; it < s.n_ins_items; it += gridDim.x) {
-    const int32_t h = s.hub_ins_hub[it];
-    if (!s.hub_moved[h]) continue;
+  for (int64_t it = blockIdx.x; it < s.n_items; it += gridDim.x) {
+    const int32_t h = s.hub_item_hub[it];
+    if (!s.hub_mv[3 * h]) continue;
+    const int32_t A = s.hub_mv[3 * h + 1], c = s.hub_mv[3 * h + 2];
     const int32_t v = s.hub_list[h];
-    const int64_t a0 = s.hub_ins_arc[it];
+    const int64_t a0 = s.hub_item_arc[it];
     const int64_t rowend = s.off[v + 1];
     const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
-    for (int64_t e = a0 + threadIdx.x; e < end; e += NT) s.flag_nxt[s.cols[e]] = 1;
+    for (int64_t e = a0 + threadIdx.x; e < end; e += NT) {
+      const int32_t u = s.cols[e];
+      if (s.mark) s.flag_nxt[u] = 1;
+      if (u == v) continue;
+      const int32_t hu = s.hub_idx[u];
+      if (hu >= 0) {
+        const int64_t w = W::get(s.w, e);
+        hub_hist_add(s, hu, A, -w);
+        hub_hist_add(s, hu, c, w);
+      }
+    }
   }
 }
 
@@ -673,17 +733,27 @@ unsigned grid_cap(int64_t blocks, int64_t cap = 152 * 16) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
-size_t warp_smem() { return (size_t)NW * WARP_CAP * 12 + (size_t)NW * 32 * 8; }
-size_t block_smem() { return (size_t)BLOCK_CAP * 12 + (size_t)NW_BLOCK * 32 * 8; }
+// Group-kernel configurations: (GROUP threads per vertex, CTA size, table slots).
+template <class V> constexpr size_t group_smem(int gpb, int cap, int ntb) {
+  return (size_t)gpb * cap * (sizeof(V) + 4) + (size_t)(ntb / 32) * 32 * 8;
+}
+template <class V> constexpr size_t warp_smem() { return group_smem<V>(8, WARP_CAP_SLOTS, 256); }
+template <class V> constexpr size_t blk1_smem() { return group_smem<V>(4, BLK1_CAP_SLOTS, 512); }
+template <class V> constexpr size_t blk2_smem() { return group_smem<V>(1, BLK2_CAP_SLOTS, 512); }
+template <class V> constexpr size_t hub_smem() { return group_smem<V>(1, HUB_CAP, HUB_NT); }
 
-template <bool LOUV, class W>
+template <bool LOUV, class W, class V>
 int set_smem_attrs() {
   static bool done = false;
   if (done) return CD_OK;
-  CD_CHECK(cudaFuncSetAttribute(k_scan_warp<LOUV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)warp_smem()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_block<LOUV, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)block_smem()));
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK2_CAP_SLOTS, B_BLK2>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk2_smem<V>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)hub_smem<V>()));
   done = true;
   return CD_OK;
 }
@@ -697,9 +767,9 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
   return b;
 }
 
-template <bool LOUV, class W>
+template <bool LOUV, class W, class V>
 int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
-  int rc = set_smem_attrs<LOUV, W>();
+  int rc = set_smem_attrs<LOUV, W, V>();
   if (rc) return rc;
   cudaStream_t st = g->stream;
   auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
@@ -707,29 +777,40 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
   auto mark = [&](int b) { marks.push_back({g->pending.size() - 1, b}); };
   if (cnt(B_HUB) > 0) {
     {
-      KTimer t(g, K_HUB_INSERT);
-      CD_LAUNCH(k_hub_insert<W><<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s));
+      KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
+      CD_LAUNCH(k_hub_clear<<<grid_cap((g->hub_slots + NT - 1) / NT, 152 * 8), NT, 0, st>>>(s, g->hub_slots));
+      CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
     {
       KTimer t(g, K_HUB_EVAL);
-      CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s, B_HUB));
+      CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) mark(B_HUB);
   }
-  if (cnt(B_BLOCK) > 0) {
+  if (cnt(B_BLK2) > 0) {
     {
-      KTimer t(g, K_SCAN_BLOCK);
-      CD_LAUNCH(k_scan_block<LOUV, W><<<grid_cap(cnt(B_BLOCK), 152 * 4), NT_BLOCK, block_smem(), st>>>(
-          s, lst(B_BLOCK), cnt(B_BLOCK), B_BLOCK));
+      KTimer t(g, K_SCAN_BLK512);
+      CD_LAUNCH((k_scan_group<LOUV, W, V, 512, 512, BLK2_CAP_SLOTS, B_BLK2>
+                 <<<grid_cap(cnt(B_BLK2), 152 * 3), 512, blk2_smem<V>(), st>>>(s, lst(B_BLK2), cnt(B_BLK2))));
     }
-    if (g->timing) mark(B_BLOCK);
+    if (g->timing) mark(B_BLK2);
+  }
+  if (cnt(B_BLK1) > 0) {
+    {
+      KTimer t(g, K_SCAN_BLK128);
+      CD_LAUNCH((k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1>
+                 <<<grid_cap((cnt(B_BLK1) + 3) / 4, 152 * 3), 512, blk1_smem<V>(), st>>>(s, lst(B_BLK1),
+                                                                                        cnt(B_BLK1))));
+    }
+    if (g->timing) mark(B_BLK1);
   }
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP);
-      CD_LAUNCH(k_scan_warp<LOUV, W><<<grid_cap((cnt(B_WARP) + NW - 1) / NW), NT, warp_smem(), st>>>(
-          s, lst(B_WARP), cnt(B_WARP), B_WARP));
+      CD_LAUNCH((k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP>
+                 <<<grid_cap((cnt(B_WARP) + NW - 1) / NW, 152 * 6), 256, warp_smem<V>(), st>>>(s, lst(B_WARP),
+                                                                                              cnt(B_WARP))));
     }
     if (g->timing) mark(B_WARP);
   }
@@ -772,9 +853,11 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
 int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out) {
   cudaStream_t st = g->stream;
   const int64_t n = g->n;
-  uint8_t* hub_moved = nullptr;
   int rc = CD_OK;
-  if (g->nhubs > 0 && (rc = dev_alloc_t(&hub_moved, g->nhubs, st))) return rc;
+  if (g->nhubs > 0) {  // histograms are built from the starting labels in round 0
+    const int32_t one = 1;
+    CD_CHECK(cudaMemcpyAsync(g->hub_build, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  }
   uint8_t* fcur = g->flag[0];
   uint8_t* fnxt = g->flag[1];
   if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fcur, 1, n, st));
@@ -788,7 +871,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (g->timing) cudaEventRecord(ev[0], st);
     CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
     if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, n, st));
-    if (hub_moved) CD_CHECK(cudaMemsetAsync(hub_moved, 0, g->nhubs, st));
+    if (g->nhubs > 0) CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
     ScanCtx s;
     s.off = g->off;
     s.cols = g->cols;
@@ -811,31 +894,44 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.round = r;
     s.tie_keep = o.tie_keep_current;
     s.singleton_rule = o.singleton_rule;
+    s.mv_a = g->mv_a;
     s.hub_list = g->bin_list + g->bin_start[B_HUB];
+    s.hub_idx = g->hub_idx;
     s.hub_tab = g->hub_tab;
-    s.hub_keys = g->hub_keys;
-    s.hub_vals = g->hub_vals;
-    s.hub_ins_hub = g->hub_ins_hub;
-    s.hub_ins_arc = g->hub_ins_arc;
+    s.hub_slot = g->hub_slot;
+    s.hub_ent_label = g->hub_ent_label;
+    s.hub_ent_w = g->hub_ent_w;
+    s.hub_ent_n = g->hub_ent_n;
+    s.hub_item_hub = g->hub_item_hub;
+    s.hub_item_arc = g->hub_item_arc;
     s.hub_ev_hub = g->hub_ev_hub;
-    s.hub_ev_slot = g->hub_ev_slot;
+    s.hub_ev_ent = g->hub_ev_ent;
     s.hub_ev_first = g->hub_ev_first;
     s.hub_part = g->hub_part;
     s.hub_cur = g->hub_cur;
     s.hub_hascur = g->hub_hascur;
     s.hub_done = g->hub_done;
-    s.hub_moved = hub_moved;
-    s.n_ins_items = g->hub_insert_items;
+    s.hub_mv = g->hub_mv;
+    s.hub_build = g->hub_build;
+    s.n_items = g->hub_items;
+    s.nhubs = g->nhubs;
     s.n_ev_items = g->hub_eval_items;
     std::vector<std::pair<size_t, int>> marks;
+    const bool v32 = g->max_degw < ((int64_t)1 << 32);
     if (louv) {
-      if (g->wkind == W_UNIT) rc = launch_round<true, WUnit>(g, s, marks);
-      else if (g->wkind == W_I32) rc = launch_round<true, WI32>(g, s, marks);
-      else rc = launch_round<true, WI64>(g, s, marks);
+      if (g->wkind == W_UNIT) rc = v32 ? launch_round<true, WUnit, uint32_t>(g, s, marks)
+                                       : launch_round<true, WUnit, unsigned long long>(g, s, marks);
+      else if (g->wkind == W_I32) rc = v32 ? launch_round<true, WI32, uint32_t>(g, s, marks)
+                                           : launch_round<true, WI32, unsigned long long>(g, s, marks);
+      else rc = v32 ? launch_round<true, WI64, uint32_t>(g, s, marks)
+                    : launch_round<true, WI64, unsigned long long>(g, s, marks);
     } else {
-      if (g->wkind == W_UNIT) rc = launch_round<false, WUnit>(g, s, marks);
-      else if (g->wkind == W_I32) rc = launch_round<false, WI32>(g, s, marks);
-      else rc = launch_round<false, WI64>(g, s, marks);
+      if (g->wkind == W_UNIT) rc = v32 ? launch_round<false, WUnit, uint32_t>(g, s, marks)
+                                       : launch_round<false, WUnit, unsigned long long>(g, s, marks);
+      else if (g->wkind == W_I32) rc = v32 ? launch_round<false, WI32, uint32_t>(g, s, marks)
+                                           : launch_round<false, WI32, unsigned long long>(g, s, marks);
+      else rc = v32 ? launch_round<false, WI64, uint32_t>(g, s, marks)
+                    : launch_round<false, WI64, unsigned long long>(g, s, marks);
     }
     if (rc) break;
     if (g->timing) cudaEventRecord(ev[1], st);
@@ -864,14 +960,21 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (moves > 0) {
       KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
       const unsigned gr = grid_cap((moves + NW - 1) / NW);
-      if (louv)
-        CD_LAUNCH(k_apply<true><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
-                                         g->sigma, g->csize, fnxt, s.mark));
-      else
-        CD_LAUNCH(k_apply<false><<<gr, NT, 0, st>>>(g->mv_v, g->mv_c, moves, g->off, g->cols, g->degw, g->C,
-                                          g->sigma, g->csize, fnxt, s.mark));
-      if (hub_moved && s.mark)
-        CD_LAUNCH(k_hub_mark<<<grid_cap(g->hub_insert_items, 152 * 8), NT, 0, st>>>(s));
+      if (louv) {
+        if (g->wkind == W_UNIT) CD_LAUNCH(k_apply<true, WUnit><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+        else if (g->wkind == W_I32) CD_LAUNCH(k_apply<true, WI32><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+        else CD_LAUNCH(k_apply<true, WI64><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+      } else {
+        if (g->wkind == W_UNIT) CD_LAUNCH(k_apply<false, WUnit><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+        else if (g->wkind == W_I32) CD_LAUNCH(k_apply<false, WI32><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+        else CD_LAUNCH(k_apply<false, WI64><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+      }
+      if (g->nhubs > 0) {
+        const unsigned gh = grid_cap(g->hub_items, 152 * 8);
+        if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, st>>>(s));
+        else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, st>>>(s));
+        else CD_LAUNCH(k_hub_mark<WI64><<<gh, NT, 0, st>>>(s));
+      }
       CD_CHECK(cudaGetLastError());
     }
     cd_round_trace tr;
@@ -897,7 +1000,6 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
   }
   if (g->timing)
     for (auto& e : ev) cudaEventDestroy(e);
-  dev_free(hub_moved, st);
   if (rc) return rc;
   int32_t stw = 0;
   CD_CHECK(cudaMemcpyAsync(&stw, g->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));

@@ -44,23 +44,25 @@ def merged(n, *edge_arrays, wmax=1, seed=0):
 
 
 def bins_graph(wmax=1):
-    """A planted-partition base plus a hub (degree > 4096), a CTA-bin vertex
-    (degree ~1000), warp-bin vertices (40..250) and isolated vertices."""
+    """A planted-partition base plus a hub (degree > 4096), vertices of
+    degree ~700 and ~2500 (the 128- and 512-thread bins), warp-bin vertices
+    (40..250) and isolated vertices."""
     rng = np.random.default_rng(5)
     n = 20000
     base = synth.sbm(n, 200, "0.03", "0.0002", seed=11)
     bu = np.repeat(np.arange(n), np.diff(base.off.numpy()))
     bv = base.cols.numpy().astype(np.int64)
     hub = (np.zeros(9000, np.int64), rng.choice(np.arange(1, 15000), 9000, replace=False))
-    blk = (np.ones(1000, np.int64), rng.choice(np.arange(2, 19000), 1000, replace=False))
+    blk = (np.ones(700, np.int64), rng.choice(np.arange(3, 19000), 700, replace=False))
+    blk2 = (np.full(2500, 2, np.int64), rng.choice(np.arange(3, 19000), 2500, replace=False))
     warp_u, warp_v = [], []
-    for x in range(2, 60):
+    for x in range(3, 60):
         k = int(rng.integers(40, 250))
         warp_u.append(np.full(k, x))
         warp_v.append(rng.choice(np.arange(60, 19000), k, replace=False))
     wu = (np.concatenate(warp_u), np.concatenate(warp_v))
     keep = (bu < 19500) & (bv < 19500)  # the last 500 vertices stay isolated
-    return merged(n, (bu[keep], bv[keep]), hub, blk, wu, wmax=wmax, seed=3)
+    return merged(n, (bu[keep], bv[keep]), hub, blk, blk2, wu, wmax=wmax, seed=3)
 
 
 def loops_graph(seed):
