@@ -15,13 +15,15 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int32_t EMPTY = -1;        // empty hash slot (labels are >= 0)
 constexpr int32_t NOCAND = INT32_MAX;  // "no candidate" community id
 
-// Degree bins of the scan (degree = row length, loops included).
-enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_BLK2, B_HUB, NBINS };
+// Degree bins of the scan (degree = row length, loops included). Vertices
+// above BLOCK_MAX ("hubs") keep persistent label histograms instead of being
+// rescanned every round.
+enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_HUB, NBINS };
 constexpr int WARP_MAX = 256;    // a warp per vertex, table <= 512 slots
 constexpr int BLK1_MAX = 1024;   // 128 threads per vertex, table <= 2048 slots
-constexpr int BLOCK_MAX = 4096;  // 512 threads per vertex, table <= 8192 slots
+constexpr int BLOCK_MAX = 1024;  // largest degree scanned through shared-memory tables
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
-constexpr int HUB_SLICE = 4096;  // histogram entries per hub evaluate item
+constexpr int HUB_SLICE = 4096;  // histogram slots per hub evaluate item
 constexpr int COL_PAD = 4;       // column arrays carry 4 spare entries for 16-byte loads
 
 // Weight kinds of the device CSR.
@@ -55,7 +57,7 @@ enum Ctr {
 // Per-kernel profiling slots.
 enum Kern {
   K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLK128,
-  K_SCAN_BLK512, K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
+  K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
   K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
@@ -76,20 +78,20 @@ struct cd_graph {
   int32_t* bin_list = nullptr;           // n vertex ids grouped by bin
   int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
   // hubs (degree > BLOCK_MAX): one persistent label histogram per hub, kept in
-  // step with the labels by the moves of its neighbours. Per hub h, capacity
-  // cap_h = 2 deg + 64 in [hub_tab[h], hub_tab[h+1]): hash slots packing
-  // (label << 32 | entry), and dense entries (label, weight).
+  // step with the labels by the moves of its neighbours: an open-addressing
+  // table of cap_h = 1.5 deg + 64 slots in [hub_tab[h], hub_tab[h+1]). A slot
+  // is one word (label << 32 | count) when every deg_w < 2^32 ("packed"),
+  // otherwise two words (label, count).
   int64_t nhubs = 0, hub_slots = 0, hub_items = 0, hub_eval_items = 0;
+  int hub_wide = 0;                        // 1: two-word slots
   int32_t* hub_idx = nullptr;              // n: hub index of a vertex, -1 otherwise
+  uint32_t* hub_bits = nullptr;            // (n+31)/32: bit v set iff v is a hub
   int64_t* hub_tab = nullptr;              // nhubs+1
-  unsigned long long* hub_slot = nullptr;  // hub_slots
-  int32_t* hub_ent_label = nullptr;        // hub_slots (-1: unused entry)
-  int64_t* hub_ent_w = nullptr;            // hub_slots
-  int32_t* hub_ent_n = nullptr;            // nhubs: entries handed out
+  unsigned long long* hub_slot = nullptr;  // hub_slots words (x2 when wide)
   int32_t* hub_item_hub = nullptr;         // per build/mark item (HUB_CHUNK arcs): hub
   int64_t* hub_item_arc = nullptr;         // per build/mark item: first arc
   int32_t* hub_ev_hub = nullptr;           // per evaluate item (HUB_SLICE entries): hub
-  int32_t* hub_ev_ent = nullptr;           // per evaluate item: first entry
+  int64_t* hub_ev_slot = nullptr;          // per evaluate item: first slot
   int64_t* hub_ev_first = nullptr;         // nhubs+1: first evaluate item of each hub
   int64_t* hub_part = nullptr;             // per evaluate item: (key hi, key lo, community)
   int64_t* hub_cur = nullptr;              // nhubs: weight into the hub's own label

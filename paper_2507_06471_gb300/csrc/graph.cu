@@ -15,9 +15,9 @@
 namespace cd {
 
 const char* const kKernelNames[K_COUNT] = {
-    "ingest",      "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
-    "scan_blk128", "scan_blk512", "hub_insert", "hub_eval",   "apply_moves", "renumber",
-    "agg_emit",    "radix_sort",  "agg_reduce", "modularity"};
+    "ingest",     "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
+    "scan_blk128", "hub_build", "hub_eval",   "apply_moves", "renumber",    "agg_emit",
+    "radix_sort", "agg_reduce", "modularity"};
 
 static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};
@@ -113,7 +113,6 @@ __device__ __forceinline__ int bin_of(int64_t d) {
   if (d <= 32) return B_T32;
   if (d <= WARP_MAX) return B_WARP;
   if (d <= BLK1_MAX) return B_BLK1;
-  if (d <= BLOCK_MAX) return B_BLK2;
   return B_HUB;
 }
 
@@ -233,9 +232,14 @@ __global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off
   }
 }
 
-__global__ void k_hub_index(const int32_t* __restrict__ hubs, int64_t nh, int32_t* hub_idx) {
+__global__ void k_hub_index(const int32_t* __restrict__ hubs, int64_t nh, int32_t* hub_idx,
+                            uint32_t* hub_bits) {
   int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (h < nh) hub_idx[hubs[h]] = (int32_t)h;
+  if (h < nh) {
+    const int32_t v = hubs[h];
+    hub_idx[v] = (int32_t)h;
+    atomicOr(&hub_bits[v >> 5], 1u << (v & 31));
+  }
 }
 
 __global__ void k_gather_rows(const int64_t* __restrict__ off, const int32_t* __restrict__ vs,
@@ -285,8 +289,8 @@ int read_status(cd_graph* g) {
 void free_arrays(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
-                g->hub_idx,      g->hub_tab,       g->hub_slot,     g->hub_ent_label, g->hub_ent_w,
-                g->hub_ent_n,    g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_ent,
+                g->hub_idx,      g->hub_bits,      g->hub_tab,       g->hub_slot,
+                g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
                 g->hub_mv,       g->hub_build,     g->C,            g->sigma,        g->csize,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
@@ -328,11 +332,11 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
     CD_CHECK(cudaMemcpyAsync(rows.data(), d_rows, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CD_CHECK(cudaStreamSynchronize(s));
     dev_free(d_rows, s);
-    std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0);
-    std::vector<int32_t> item_hub, ev_hub, ev_ent;
+    std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0), ev_slot;
+    std::vector<int32_t> item_hub, ev_hub;
     for (int64_t h = 0; h < nh; ++h) {
       int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
-      int64_t cap = 2 * deg + 64;  // live labels <= deg; the rest absorbs labels that come and go
+      int64_t cap = deg + deg / 2 + 64;  // live labels <= deg; the rest absorbs labels that come and go
       tab[h + 1] = tab[h] + cap;
       for (int64_t a = 0; a < deg; a += HUB_CHUNK) {
         item_hub.push_back((int32_t)h);
@@ -341,7 +345,7 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
       ev_first[h] = (int64_t)ev_hub.size();
       for (int64_t e = 0; e < cap; e += HUB_SLICE) {
         ev_hub.push_back((int32_t)h);
-        ev_ent.push_back((int32_t)e);
+        ev_slot.push_back(e);
       }
     }
     ev_first[nh] = (int64_t)ev_hub.size();
@@ -349,15 +353,14 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
     g->hub_items = (int64_t)item_hub.size();
     g->hub_eval_items = (int64_t)ev_hub.size();
     if ((rc = dev_alloc_t(&g->hub_idx, g->n, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_bits, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_slot, g->hub_slots, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ent_label, g->hub_slots, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ent_w, g->hub_slots, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ent_n, nh, s))) return rc;
+    g->hub_wide = g->max_degw >= ((int64_t)1 << 32) ? 1 : 0;
+    if ((rc = dev_alloc_t(&g->hub_slot, g->hub_slots * (1 + g->hub_wide), s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_item_hub, g->hub_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_item_arc, g->hub_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_ev_hub, g->hub_eval_items, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ev_ent, g->hub_eval_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ev_slot, g->hub_eval_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_ev_first, nh + 1, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_part, 3 * g->hub_eval_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_cur, nh, s))) return rc;
@@ -369,14 +372,15 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
     CD_CHECK(cudaMemcpyAsync(g->hub_item_hub, item_hub.data(), item_hub.size() * 4, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_arc, item_arc.data(), item_arc.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_hub, ev_hub.data(), ev_hub.size() * 4, cudaMemcpyHostToDevice, s));
-    CD_CHECK(cudaMemcpyAsync(g->hub_ev_ent, ev_ent.data(), ev_ent.size() * 4, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_ev_slot, ev_slot.data(), ev_slot.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_first, ev_first.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_idx, 0xff, g->n * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_bits, 0, (g->n + 31) / 32 * 4, s));
     CD_LAUNCH(k_hub_index<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
-                                                                       g->hub_idx));
+                                                                       g->hub_idx, g->hub_bits));
     CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
   }
   dev_free(d_base, s);

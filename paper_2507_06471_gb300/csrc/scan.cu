@@ -28,7 +28,6 @@ constexpr int NT = 256;  // threads of the tile and hub-evaluate kernels
 constexpr int NW = NT / 32;
 constexpr int WARP_CAP_SLOTS = 2 * WARP_MAX;   // table slots per warp-bin vertex
 constexpr int BLK1_CAP_SLOTS = 2 * BLK1_MAX;   // per 128-thread group
-constexpr int BLK2_CAP_SLOTS = 2 * BLOCK_MAX;  // per 512-thread CTA
 
 // ------------------------------------------------------------------ coin
 
@@ -101,15 +100,14 @@ struct ScanCtx {
   // hubs
   const int32_t* hub_list;
   const int32_t* hub_idx;
+  const uint32_t* hub_bits;
   const int64_t* hub_tab;
   unsigned long long* hub_slot;
-  int32_t* hub_ent_label;
-  int64_t* hub_ent_w;
-  int32_t* hub_ent_n;
+  int hub_wide;
   const int32_t* hub_item_hub;
   const int64_t* hub_item_arc;
   const int32_t* hub_ev_hub;
-  const int32_t* hub_ev_ent;
+  const int64_t* hub_ev_slot;
   const int64_t* hub_ev_first;
   int64_t* hub_part;
   int64_t* hub_cur;
@@ -204,6 +202,78 @@ __device__ __forceinline__ int64_t group_sum(unsigned peers, int64_t wt, int64_t
   }
 }
 
+// ------------------------------------------------------------------ hub histograms
+
+constexpr unsigned long long SLOT_EMPTY = ~0ull;
+
+// k_{h,label} += w in hub h's histogram (w may be negative: a neighbour left
+// `label`; the count then stays >= 0). A packed slot is updated with one
+// 64-bit atomic: the count lives in the low word and never carries or borrows
+// into the label. If no slot is free, or a label to decrement is missing
+// (only possible after a lost update), the rebuild flag is raised.
+__device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
+  const int64_t base = s.hub_tab[h];
+  const int64_t cap = s.hub_tab[h + 1] - base;
+  int64_t slot = (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
+  if (!s.hub_wide) {
+    unsigned long long* words = s.hub_slot + base;
+    for (int64_t probe = 0; probe < cap; ++probe) {
+      unsigned long long cur = words[slot];
+      if (cur == SLOT_EMPTY) {
+        if (w <= 0) break;
+        cur = atomicCAS(&words[slot], SLOT_EMPTY,
+                        ((unsigned long long)(uint32_t)label << 32) | (unsigned long long)(uint32_t)w);
+        if (cur == SLOT_EMPTY) return;
+      }
+      if ((int32_t)(cur >> 32) == label) {
+        atomicAdd(&words[slot], (unsigned long long)w);
+        return;
+      }
+      slot = slot + 1 == cap ? 0 : slot + 1;
+    }
+  } else {
+    unsigned long long* words = s.hub_slot + 2 * base;  // (label, count) pairs
+    for (int64_t probe = 0; probe < cap; ++probe) {
+      unsigned long long cur = words[2 * slot];
+      if (cur == SLOT_EMPTY) {
+        if (w <= 0) break;
+        cur = atomicCAS(&words[2 * slot], SLOT_EMPTY, (unsigned long long)(uint32_t)label);
+        if (cur == SLOT_EMPTY) cur = (uint32_t)label;
+      }
+      if ((int32_t)(uint32_t)cur == label) {
+        atomicAdd(&words[2 * slot + 1], (unsigned long long)w);
+        return;
+      }
+      slot = slot + 1 == cap ? 0 : slot + 1;
+    }
+  }
+  atomicExch(s.hub_build, 1);  // rebuild before the next scan
+}
+
+// Read slot i of a hub table at `base`: (label or -1 if empty, count).
+__device__ __forceinline__ void hub_slot_read(const ScanCtx& s, int64_t base, int64_t i, int32_t& c,
+                                              int64_t& k) {
+  if (!s.hub_wide) {
+    const unsigned long long x = s.hub_slot[base + i];
+    c = x == SLOT_EMPTY ? -1 : (int32_t)(x >> 32);
+    k = (int64_t)(x & 0xffffffffull);
+  } else {
+    const unsigned long long x = s.hub_slot[2 * (base + i)];
+    c = x == SLOT_EMPTY ? -1 : (int32_t)(uint32_t)x;
+    k = (int64_t)s.hub_slot[2 * (base + i) + 1];
+  }
+}
+
+// A committed move of a neighbour of u (label A -> c over an arc of weight
+// w) changes u's histogram if u is a hub. The hub bitmap (n bits) stays in L2.
+__device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u, int32_t A, int32_t c,
+                                                    int64_t w) {
+  if (!((__ldg(&s.hub_bits[u >> 5]) >> (u & 31)) & 1u)) return;
+  const int32_t h = s.hub_idx[u];
+  hub_hist_add(s, h, A, -w);
+  hub_hist_add(s, h, c, w);
+}
+
 // ------------------------------------------------------------------ tiles
 
 // TILE lanes per vertex, one arc per lane (degree <= TILE).
@@ -269,6 +339,7 @@ __global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __re
       if (commit && has) s.flag_nxt[u] = 1;  // the neighbours of a moved vertex
       if (want && sub == 0) s.flag_nxt[v] = 1;
     }
+    if (s.nhubs > 0 && commit && cand) hub_neighbour_moved(s, u, cur, target, wt);
     if (sub == 0 && act) {
       ++n_act;
       n_arcs += d;
@@ -282,16 +353,19 @@ __global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __re
 // ------------------------------------------------------------------ shared-memory tables
 
 // Open addressing with linear probing; capacity 2^lg >= 2 x the arcs inserted,
-// so a free slot is always found within `cap` probes.
+// so a free slot is always found within `cap` probes. A newly claimed slot is
+// appended to the table's occupied list, so that reading the table costs the
+// number of distinct labels rather than its capacity.
 template <class V>
-__device__ __forceinline__ void smem_insert(int32_t* keys, V* vals, unsigned lg, int32_t key, V w,
-                                            int32_t* status) {
+__device__ __forceinline__ void smem_insert(int32_t* keys, V* vals, uint16_t* occ, int* occ_n,
+                                            unsigned lg, int32_t key, V w, int32_t* status) {
   const unsigned mask = (1u << lg) - 1u;
   unsigned h = ((uint32_t)key * 2654435761u) >> (32 - lg);
   for (unsigned probe = 0; probe <= mask; ++probe) {
     const int32_t prev = atomicCAS(&keys[h], EMPTY, key);
     if (prev == EMPTY || prev == key) {
       atomicAdd(vals + h, w);
+      if (prev == EMPTY) occ[atomicAdd(occ_n, 1)] = (uint16_t)h;
       return;
     }
     h = (h + 1) & mask;
@@ -324,8 +398,8 @@ __device__ __forceinline__ void group_sync(int gid) {
 // before `end` stays inside the allocation.
 template <class W, class V, int GROUP>
 __device__ __forceinline__ void group_insert(const ScanCtx& s, int32_t v, int64_t beg, int64_t end,
-                                             int gl, int32_t* keys, V* vals, unsigned lg,
-                                             int64_t* stage) {
+                                             int gl, int32_t* keys, V* vals, uint16_t* occ, int* occ_n,
+                                             unsigned lg, int64_t* stage) {
   const int lane = threadIdx.x & 31;
   const int wig = gl >> 5;
   const int64_t a0 = beg & ~(int64_t)3;
@@ -347,23 +421,25 @@ __device__ __forceinline__ void group_insert(const ScanCtx& s, int32_t v, int64_
     for (int j = 0; j < 4; ++j) {
       const unsigned peers = __match_any_sync(FULL, lbl[j]);
       const int64_t gsum = group_sum<W>(peers, wt[j], stage);
-      if (lbl[j] >= 0 && (__ffs(peers) - 1) == lane) smem_insert(keys, vals, lg, lbl[j], (V)gsum, s.status);
+      if (lbl[j] >= 0 && (__ffs(peers) - 1) == lane)
+        smem_insert(keys, vals, occ, occ_n, lg, lbl[j], (V)gsum, s.status);
     }
   }
 }
 
-// Scan a group's table: take every occupied slot as a candidate, clear it.
+// Read a group's table through its occupied list: every listed slot is a
+// candidate; the slot is cleared for the next vertex.
 template <bool LOUV, class V, int GROUP>
 __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_t dv, int gl,
-                                           int32_t* keys, V* vals, int cap,
+                                           int32_t* keys, V* vals, const uint16_t* occ, int nocc,
                                            typename KeyOf<LOUV>::T& bk, int32_t& bc, bool& hc,
                                            int64_t& kc, int64_t& ncand) {
-  for (int j = gl; j < cap; j += GROUP) {
-    const int32_t c = keys[j];
-    if (c == EMPTY) continue;
-    const int64_t k = (int64_t)vals[j];
-    keys[j] = EMPTY;
-    vals[j] = 0;
+  for (int j = gl; j < nocc; j += GROUP) {
+    const int slot = occ[j];
+    const int32_t c = keys[slot];
+    const int64_t k = (int64_t)vals[slot];
+    keys[slot] = EMPTY;
+    vals[slot] = 0;
     ++ncand;
     if (c == cur) {
       hc = true;
@@ -391,15 +467,20 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
   __shared__ int32_t red_c[GPB][WPG];
   __shared__ int64_t red_kc[GPB][WPG];
   __shared__ int32_t red_hc[GPB][WPG];
+  __shared__ int occ_n[GPB];
+  __shared__ int32_t moved_to[GPB];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int gid = threadIdx.x / GROUP, gl = threadIdx.x % GROUP, wig = gl >> 5;
   V* vals = (V*)smem + (size_t)gid * CAP;
   int32_t* keys = (int32_t*)(smem + (size_t)GPB * CAP * sizeof(V)) + (size_t)gid * CAP;
   int64_t* stage = (int64_t*)(smem + (size_t)GPB * CAP * (sizeof(V) + 4)) + wid * 32;
+  uint16_t* occ = (uint16_t*)(smem + (size_t)GPB * CAP * (sizeof(V) + 4) + (size_t)(NTB / 32) * 32 * 8) +
+                  (size_t)gid * CAP;
   for (int j = gl; j < CAP; j += GROUP) {
     keys[j] = EMPTY;
     vals[j] = 0;
   }
+  if (gl == 0) occ_n[gid] = 0;
   group_sync<GROUP, NTB>(gid);
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
   for (int64_t i = (int64_t)blockIdx.x * GPB + gid; i < count; i += (int64_t)gridDim.x * GPB) {
@@ -409,14 +490,15 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
     const int64_t d = end - beg;
     const unsigned lg = ceil_log2(2 * d);
     const int32_t cur = s.C[v];
-    group_insert<W, V, GROUP>(s, v, beg, end, gl, keys, vals, lg, stage);
+    group_insert<W, V, GROUP>(s, v, beg, end, gl, keys, vals, occ, &occ_n[gid], lg, stage);
     group_sync<GROUP, NTB>(gid);
     const int64_t dv = LOUV ? s.degw[v] : 0;
+    const int nocc = occ_n[gid];
     K bk = K(0);
     int32_t bc = NOCAND;
     bool hc = false;
     int64_t kc = 0;
-    group_eval<LOUV, V, GROUP>(s, cur, dv, gl, keys, vals, 1 << lg, bk, bc, hc, kc, n_cand);
+    group_eval<LOUV, V, GROUP>(s, cur, dv, gl, keys, vals, occ, nocc, bk, bc, hc, kc, n_cand);
     reduce_best(bk, bc, 32);
     unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
@@ -438,11 +520,23 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
     }
     if (gl == 0) {
       const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc);
-      n_def += act_single(s, v, cur, target);
+      const int def = act_single(s, v, cur, target);
+      n_def += def;
       ++n_act;
       n_arcs += d;
+      occ_n[gid] = 0;
+      moved_to[gid] = (target != cur && !def) ? target : -1;
     }
-    group_sync<GROUP, NTB>(gid);  // tables and reduction slots are reused
+    group_sync<GROUP, NTB>(gid);  // tables and reduction slots are reused after this
+    // a committed move: flag the neighbours for the next round and update the
+    // histograms of neighbouring hubs (their evaluation for this round is done)
+    const int32_t to = moved_to[gid];
+    if (to >= 0 && (s.mark || s.nhubs > 0))
+      for (int64_t e = beg + gl; e < end; e += GROUP) {
+        const int32_t u = s.cols[e];
+        if (s.mark) s.flag_nxt[u] = 1;
+        if (s.nhubs > 0 && u != v) hub_neighbour_moved(s, u, cur, to, W::get(s.w, e));
+      }
   }
   flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def);
 }
@@ -454,52 +548,18 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
 // committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
 // therefore reads its distinct labels instead of its whole row.
 
-constexpr unsigned long long SLOT_EMPTY = ~0ull;
-
-// k_{h,label} += w in hub h's histogram. A label not present takes the next
-// dense entry and publishes (label << 32 | entry) in its hash slot; an entry
-// lost to a concurrent insert of the same label stays unused (label -1). If
-// the entries run out, the rebuild flag is raised.
-__device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
-  const int64_t base = s.hub_tab[h];
-  const int64_t cap = s.hub_tab[h + 1] - base;
-  unsigned long long* slots = s.hub_slot + base;
-  int64_t slot = (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
-  for (int64_t probe = 0; probe < cap; ++probe) {
-    unsigned long long cur = slots[slot];
-    if (cur == SLOT_EMPTY) {
-      const int32_t e = atomicAdd(&s.hub_ent_n[h], 1);
-      if (e >= cap) {
-        atomicExch(s.hub_build, 1);
-        return;
-      }
-      const unsigned long long mine = ((unsigned long long)(uint32_t)label << 32) | (uint32_t)e;
-      cur = atomicCAS(&slots[slot], SLOT_EMPTY, mine);
-      if (cur == SLOT_EMPTY) {
-        s.hub_ent_label[base + e] = label;
-        atomicAdd((unsigned long long*)&s.hub_ent_w[base + e], (unsigned long long)w);
-        return;
-      }
-    }
-    if ((int32_t)(cur >> 32) == label) {
-      atomicAdd((unsigned long long*)&s.hub_ent_w[base + (uint32_t)cur], (unsigned long long)w);
-      return;
-    }
-    slot = slot + 1 == cap ? 0 : slot + 1;
-  }
-  atomicExch(s.hub_build, 1);  // no free slot: rebuild before the next scan
-}
-
 // Clear every hub histogram when a rebuild is due (flag set).
 __global__ void __launch_bounds__(NT) k_hub_clear(ScanCtx s, int64_t slots) {
   if (!*(volatile int32_t*)s.hub_build) return;
   const int64_t stride = (int64_t)gridDim.x * NT;
   for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < slots; i += stride) {
-    s.hub_slot[i] = SLOT_EMPTY;
-    s.hub_ent_label[i] = -1;
-    s.hub_ent_w[i] = 0;
+    if (!s.hub_wide) {
+      s.hub_slot[i] = SLOT_EMPTY;
+    } else {
+      s.hub_slot[2 * i] = SLOT_EMPTY;
+      s.hub_slot[2 * i + 1] = 0;
+    }
   }
-  for (int64_t h = (int64_t)blockIdx.x * NT + threadIdx.x; h < s.nhubs; h += stride) s.hub_ent_n[h] = 0;
 }
 
 constexpr int HUB_NT = 512;
@@ -512,13 +572,16 @@ template <class W, class V>
 __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
   if (!*(volatile int32_t*)s.hub_build) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int occ_n;
   V* vals = (V*)smem;
   int32_t* keys = (int32_t*)(smem + (size_t)HUB_CAP * sizeof(V));
   int64_t* stage = (int64_t*)(smem + (size_t)HUB_CAP * (sizeof(V) + 4)) + (threadIdx.x >> 5) * 32;
+  uint16_t* occ = (uint16_t*)(smem + (size_t)HUB_CAP * (sizeof(V) + 4) + (size_t)(HUB_NT / 32) * 32 * 8);
   for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {
     keys[j] = EMPTY;
     vals[j] = 0;
   }
+  if (threadIdx.x == 0) occ_n = 0;
   __syncthreads();
   for (int64_t it = blockIdx.x; it < s.n_items; it += gridDim.x) {
     const int32_t h = s.hub_item_hub[it];
@@ -526,16 +589,19 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
     const int64_t a0 = s.hub_item_arc[it];
     const int64_t rowend = s.off[v + 1];
     const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
-    group_insert<W, V, HUB_NT>(s, v, a0, end, threadIdx.x, keys, vals, 13, stage);
+    group_insert<W, V, HUB_NT>(s, v, a0, end, threadIdx.x, keys, vals, occ, &occ_n, 13, stage);
     __syncthreads();
-    for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {
-      const int32_t c = keys[j];
-      if (c == EMPTY) continue;
-      const int64_t k = (int64_t)vals[j];
-      keys[j] = EMPTY;
-      vals[j] = 0;
+    const int nocc = occ_n;
+    for (int j = threadIdx.x; j < nocc; j += HUB_NT) {
+      const int slot = occ[j];
+      const int32_t c = keys[slot];
+      const int64_t k = (int64_t)vals[slot];
+      keys[slot] = EMPTY;
+      vals[slot] = 0;
       hub_hist_add(s, h, c, k);
     }
+    __syncthreads();
+    if (threadIdx.x == 0) occ_n = 0;
     __syncthreads();
   }
 }
@@ -560,27 +626,34 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
     const int64_t dv = LOUV ? s.degw[v] : 0;
     const int64_t base = s.hub_tab[h];
     const int64_t cap = s.hub_tab[h + 1] - base;
-    int64_t cnt = s.hub_ent_n[h];
-    cnt = cnt < cap ? cnt : cap;
-    const int64_t e0 = s.hub_ev_ent[it];
-    const int64_t e1 = e0 + HUB_SLICE < cnt ? e0 + HUB_SLICE : cnt;
+    const int64_t e0 = s.hub_ev_slot[it];
+    const int64_t e1 = e0 + HUB_SLICE < cap ? e0 + HUB_SLICE : cap;
     K bk = K(0);
     int32_t bc = NOCAND;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += NT) {
-      const int32_t c = s.hub_ent_label[base + e];
-      if (c < 0) continue;
-      const int64_t k = s.hub_ent_w[base + e];
-      if (k == 0) continue;
-      ++n_cand;
-      if (c == cur) {
-        s.hub_cur[h] = k;
-        s.hub_hascur[h] = 1;
-        if (LOUV) continue;
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += 4 * NT) {
+      int32_t c[4];
+      int64_t k[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // issue the four slot loads first
+        const int64_t x = e + (int64_t)j * NT;
+        c[j] = -1;
+        k[j] = 0;
+        if (x < e1) hub_slot_read(s, base, x, c[j], k[j]);
       }
-      const K key = cand_key<LOUV>(s, c, k, dv);
-      if (better(key, c, bk, bc)) {
-        bk = key;
-        bc = c;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (c[j] < 0 || k[j] == 0) continue;  // unused entry, or a label that left
+        ++n_cand;
+        if (c[j] == cur) {
+          s.hub_cur[h] = k[j];
+          s.hub_hascur[h] = 1;
+          if (LOUV) continue;
+        }
+        const K key = cand_key<LOUV>(s, c[j], k[j], dv);
+        if (better(key, c[j], bk, bc)) {
+          bk = key;
+          bc = c[j];
+        }
       }
     }
     reduce_best(bk, bc, 32);
@@ -640,44 +713,25 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
 
 // ------------------------------------------------------------------ apply
 
-// Warp per committed move (vertex v: A -> c): new label, Sigma_tot and
-// community sizes (Louvain); next-round flags of the neighbours of vertices
-// with 33..BLOCK_MAX arcs (tile kernels flag their own, hubs are handled by
-// k_hub_mark); and the histograms of the hubs among v's neighbours.
-template <bool LOUV, class W>
-__global__ void __launch_bounds__(NT) k_apply(ScanCtx s, int64_t nmoves, int64_t* sigma,
-                                              int32_t* csize, int32_t* C) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-  for (int64_t m = warp; m < nmoves; m += nwarps) {
-    const int32_t v = s.mv_v[m], c = s.mv_c[m], A = s.mv_a[m];
-    if (lane == 0) {
-      if (LOUV) {
-        const int64_t d = s.degw[v];
-        atomicAdd((unsigned long long*)&sigma[A], (unsigned long long)(-d));
-        atomicAdd((unsigned long long*)&sigma[c], (unsigned long long)d);
-        atomicSub(&csize[A], 1);
-        atomicAdd(&csize[c], 1);
-      }
-      C[v] = c;
+// Thread per committed move (vertex v: A -> c): the new label, and Sigma_tot
+// and community sizes for Louvain. (The scan kernels flag the neighbours of
+// their committed vertices and update neighbouring hub histograms; moved hubs
+// are handled by k_hub_mark.)
+template <bool LOUV>
+__global__ void __launch_bounds__(NT) k_apply_state(ScanCtx s, int64_t nmoves, int64_t* sigma,
+                                                    int32_t* csize, int32_t* C) {
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < nmoves; m += stride) {
+    const int32_t v = s.mv_v[m], c = s.mv_c[m];
+    if (LOUV) {
+      const int32_t A = s.mv_a[m];
+      const int64_t d = s.degw[v];
+      atomicAdd((unsigned long long*)&sigma[A], (unsigned long long)(-d));
+      atomicAdd((unsigned long long*)&sigma[c], (unsigned long long)d);
+      atomicSub(&csize[A], 1);
+      atomicAdd(&csize[c], 1);
     }
-    const int64_t beg = s.off[v], end = s.off[v + 1];
-    if (end - beg > BLOCK_MAX) continue;  // a hub: k_hub_mark
-    const bool flag = s.mark && end - beg > 32;
-    if (!flag && s.nhubs == 0) continue;
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      const int32_t u = s.cols[e];
-      if (flag) s.flag_nxt[u] = 1;
-      if (s.nhubs > 0 && u != v) {
-        const int32_t h = s.hub_idx[u];
-        if (h >= 0) {
-          const int64_t w = W::get(s.w, e);
-          hub_hist_add(s, h, A, -w);
-          hub_hist_add(s, h, c, w);
-        }
-      }
-    }
+    C[v] = c;
   }
 }
 
@@ -697,12 +751,7 @@ __global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
       const int32_t u = s.cols[e];
       if (s.mark) s.flag_nxt[u] = 1;
       if (u == v) continue;
-      const int32_t hu = s.hub_idx[u];
-      if (hu >= 0) {
-        const int64_t w = W::get(s.w, e);
-        hub_hist_add(s, hu, A, -w);
-        hub_hist_add(s, hu, c, w);
-      }
+      hub_neighbour_moved(s, u, A, c, W::get(s.w, e));
     }
   }
 }
@@ -735,11 +784,10 @@ unsigned grid_cap(int64_t blocks, int64_t cap = 152 * 16) {
 
 // Group-kernel configurations: (GROUP threads per vertex, CTA size, table slots).
 template <class V> constexpr size_t group_smem(int gpb, int cap, int ntb) {
-  return (size_t)gpb * cap * (sizeof(V) + 4) + (size_t)(ntb / 32) * 32 * 8;
+  return (size_t)gpb * cap * (sizeof(V) + 4) + (size_t)(ntb / 32) * 32 * 8 + (size_t)gpb * cap * 2;
 }
 template <class V> constexpr size_t warp_smem() { return group_smem<V>(8, WARP_CAP_SLOTS, 256); }
 template <class V> constexpr size_t blk1_smem() { return group_smem<V>(4, BLK1_CAP_SLOTS, 512); }
-template <class V> constexpr size_t blk2_smem() { return group_smem<V>(1, BLK2_CAP_SLOTS, 512); }
 template <class V> constexpr size_t hub_smem() { return group_smem<V>(1, HUB_CAP, HUB_NT); }
 
 template <bool LOUV, class W, class V>
@@ -750,8 +798,6 @@ int set_smem_attrs() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK2_CAP_SLOTS, B_BLK2>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk2_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
   done = true;
@@ -787,14 +833,6 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
       CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) mark(B_HUB);
-  }
-  if (cnt(B_BLK2) > 0) {
-    {
-      KTimer t(g, K_SCAN_BLK512);
-      CD_LAUNCH((k_scan_group<LOUV, W, V, 512, 512, BLK2_CAP_SLOTS, B_BLK2>
-                 <<<grid_cap(cnt(B_BLK2), 152 * 3), 512, blk2_smem<V>(), st>>>(s, lst(B_BLK2), cnt(B_BLK2))));
-    }
-    if (g->timing) mark(B_BLK2);
   }
   if (cnt(B_BLK1) > 0) {
     {
@@ -897,15 +935,14 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.mv_a = g->mv_a;
     s.hub_list = g->bin_list + g->bin_start[B_HUB];
     s.hub_idx = g->hub_idx;
+    s.hub_bits = g->hub_bits;
     s.hub_tab = g->hub_tab;
     s.hub_slot = g->hub_slot;
-    s.hub_ent_label = g->hub_ent_label;
-    s.hub_ent_w = g->hub_ent_w;
-    s.hub_ent_n = g->hub_ent_n;
+    s.hub_wide = g->hub_wide;
     s.hub_item_hub = g->hub_item_hub;
     s.hub_item_arc = g->hub_item_arc;
     s.hub_ev_hub = g->hub_ev_hub;
-    s.hub_ev_ent = g->hub_ev_ent;
+    s.hub_ev_slot = g->hub_ev_slot;
     s.hub_ev_first = g->hub_ev_first;
     s.hub_part = g->hub_part;
     s.hub_cur = g->hub_cur;
@@ -959,16 +996,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     }
     if (moves > 0) {
       KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
-      const unsigned gr = grid_cap((moves + NW - 1) / NW);
-      if (louv) {
-        if (g->wkind == W_UNIT) CD_LAUNCH(k_apply<true, WUnit><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-        else if (g->wkind == W_I32) CD_LAUNCH(k_apply<true, WI32><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-        else CD_LAUNCH(k_apply<true, WI64><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-      } else {
-        if (g->wkind == W_UNIT) CD_LAUNCH(k_apply<false, WUnit><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-        else if (g->wkind == W_I32) CD_LAUNCH(k_apply<false, WI32><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-        else CD_LAUNCH(k_apply<false, WI64><<<gr, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-      }
+      const unsigned gt = grid_cap((moves + NT - 1) / NT);
+      if (louv)
+        CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+      else
+        CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
       if (g->nhubs > 0) {
         const unsigned gh = grid_cap(g->hub_items, 152 * 8);
         if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, st>>>(s));

@@ -44,9 +44,10 @@ def merged(n, *edge_arrays, wmax=1, seed=0):
 
 
 def bins_graph(wmax=1):
-    """A planted-partition base plus a hub (degree > 4096), vertices of
-    degree ~700 and ~2500 (the 128- and 512-thread bins), warp-bin vertices
-    (40..250) and isolated vertices."""
+    """A planted-partition base plus hubs of degree ~9000 (several build
+    chunks and evaluate slices) and ~2500 (one of each), a vertex of degree
+    ~700 (128 threads per vertex), warp-bin vertices (40..250) and isolated
+    vertices."""
     rng = np.random.default_rng(5)
     n = 20000
     base = synth.sbm(n, 200, "0.03", "0.0002", seed=11)
@@ -306,3 +307,34 @@ def test_device_generator_matches_host():
     gh = synth.rmat(11, 16, seed=5)
     gd = synth.rmat(11, 16, seed=5, device="cuda")
     assert torch.equal(gh.off, gd.off.cpu()) and torch.equal(gh.cols, gd.cols.cpu())
+
+
+def test_wide_hub_histograms():
+    # A hub whose weighted degree exceeds 2^32 makes the library keep hub
+    # histograms in two-word slots (label, count); results must not change.
+    rng = np.random.default_rng(12)
+    n = 4000
+    base = synth.sbm(n, 40, "0.05", "0.001", seed=13)
+    bu = np.repeat(np.arange(n), np.diff(base.off.numpy()))
+    bv = base.cols.numpy().astype(np.int64)
+    keep = bu < bv
+    edges = list(zip(bu[keep].tolist(), bv[keep].tolist()))
+    ws = rng.integers(1, 5, len(edges)).tolist()
+    leaves = rng.choice(np.arange(1, n), 1500, replace=False)
+    have = set(edges)
+    for x in leaves.tolist():
+        if (0, x) not in have:
+            edges.append((0, x))
+            ws.append(int(rng.integers(2**30, 2**31 - 1)))
+    g = synth.from_edge_list(n, edges, ws)
+    off, cols, w = g.numpy()
+    d, vol = oracle.degw(off, cols, w)
+    assert d.max() >= 2**32
+    G = upload(g)
+    lab, rounds = G.lpa()
+    olab, otr = oracle.lpa(off, cols, w)
+    assert rounds == otr.rounds and np.array_equal(lab.cpu().numpy(), olab)
+    lab, levels, q = G.louvain()
+    olab, olv, oq, _ = oracle.louvain(off, cols, w)
+    assert levels == olv and np.array_equal(lab.cpu().numpy(), olab)
+    assert abs(q - oq) <= 1e-12 * max(1.0, abs(oq))
