@@ -149,6 +149,30 @@ int cd_modularity(cd_graph* g, const int32_t* labels, int on_device, double* q_o
 int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
                    int32_t* levels_out, double* q_out);
 
+/* Batched mode (Algorithms 1-3 applied to many graphs at once). Declare that
+ * g is n_graphs independent graphs packed block-diagonally: graph b owns the
+ * vertices [vstart[b], vstart[b+1]) (vstart: n_graphs+1 int64, vstart[0] = 0,
+ * vstart[n_graphs] = n, host or device per on_device) and no arc may leave
+ * its block (CD_EINVAL otherwise). The cd_batch_* calls then solve every
+ * graph exactly as a solo run of that graph would (same labels): gains use
+ * the graph's own vol(V), the deferral coin uses ids local to the graph, and
+ * stop tests are per graph. Other calls on g still treat it as one graph. */
+int cd_graph_set_batches(cd_graph* g, const int64_t* vstart, int64_t n_graphs, int on_device);
+
+/* Algorithm 1 on every graph of a batched g. labels_out: n int32, labels as
+ * graph-local vertex ids; rounds_out (host, n_graphs int32, may be NULL):
+ * each graph's round count (it stops after its own round with
+ * moved + deferred <= threshold). */
+int cd_batch_lpa_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
+                     int32_t* rounds_out);
+
+/* Algorithm 3 on every graph of a batched g, levels in lockstep (a graph that
+ * is done stays frozen). labels_out: n int32, each graph's communities
+ * numbered 0..k_b-1; levels_out and q_out (host, n_graphs, may be NULL): each
+ * graph's level count and modularity (Sec. II-C) on its own graph. */
+int cd_batch_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
+                         int32_t* levels_out, double* q_out);
+
 /* Copy up to cap per-round records of the last run on g into out; *count
  * receives the number of records available. */
 int cd_trace_get(const cd_graph* g, cd_round_trace* out, int32_t cap, int32_t* count);

@@ -27,7 +27,8 @@ EXPORTED = [
     "cd_params_default", "cd_csr_upload", "cd_graph_free", "cd_graph_info", "cd_graph_download",
     "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
     "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
-    "cd_launch_count", "cd_modularity_noalloc",
+    "cd_launch_count", "cd_modularity_noalloc", "cd_graph_set_batches", "cd_batch_lpa_run",
+    "cd_batch_louvain_run",
 ]
 
 
@@ -86,6 +87,9 @@ def lib():
         L.cd_launch_count.restype = ctypes.c_int64
         L.cd_launch_count.argtypes = []
         L.cd_modularity_noalloc.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]
+        L.cd_graph_set_batches.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int]
+        L.cd_batch_lpa_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P]
+        L.cd_batch_louvain_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P, _P]
         _lib = L
     return _lib
 
@@ -235,6 +239,28 @@ def cd_modularity_noalloc(offsets, cols, w, labels, n: Optional[int] = None, str
     return q.value
 
 
+def cd_graph_set_batches(g, vstart) -> None:
+    """vstart: int64 array of n_graphs+1 vertex offsets (host numpy or device tensor)."""
+    p, dev = _ptr(vstart)
+    _check(lib().cd_graph_set_batches(g, p, int(len(vstart)) - 1, dev), "cd_graph_set_batches")
+
+
+def cd_batch_lpa_run(g, params: cd_params, labels_out, n_graphs: int):
+    p, dev = _ptr(labels_out)
+    rounds = np.zeros(n_graphs, dtype=np.int32)
+    _check(lib().cd_batch_lpa_run(g, ctypes.byref(params), p, dev, _ptr(rounds)[0]), "cd_batch_lpa_run")
+    return rounds
+
+
+def cd_batch_louvain_run(g, params: cd_params, labels_out, n_graphs: int):
+    p, dev = _ptr(labels_out)
+    levels = np.zeros(n_graphs, dtype=np.int32)
+    q = np.zeros(n_graphs, dtype=np.float64)
+    _check(lib().cd_batch_louvain_run(g, ctypes.byref(params), p, dev, _ptr(levels)[0], _ptr(q)[0]),
+           "cd_batch_louvain_run")
+    return levels, q
+
+
 def cd_launch_count() -> int:
     return int(lib().cd_launch_count())
 
@@ -305,6 +331,22 @@ class Graph:
 
     def download(self):
         return cd_graph_download(self.h)
+
+    def set_batches(self, vstart):
+        cd_graph_set_batches(self.h, vstart)
+        self.n_graphs = int(len(vstart)) - 1
+
+    def batch_lpa(self, params=None, device="cuda", **kw):
+        params = params or cd_params_default(**kw)
+        lab = self._labels(device)
+        rounds = cd_batch_lpa_run(self.h, params, lab, self.n_graphs)
+        return lab, rounds
+
+    def batch_louvain(self, params=None, device="cuda", **kw):
+        params = params or cd_params_default(**kw)
+        lab = self._labels(device)
+        levels, q = cd_batch_louvain_run(self.h, params, lab, self.n_graphs)
+        return lab, levels, q
 
     def trace(self):
         return cd_trace_get(self.h)

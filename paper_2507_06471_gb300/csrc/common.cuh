@@ -113,6 +113,16 @@ struct cd_graph {
   int64_t* h_ctr = nullptr;    // pinned host copy
   int32_t* status = nullptr;   // device status word (0 = ok)
 
+  // batched mode: independent graphs packed block-diagonally (graph b owns
+  // vertices [gbase[b], gbase[b+1]) and no arc leaves its block)
+  int64_t nb = 0;                  // number of graphs (0: not batched)
+  int32_t* gid = nullptr;          // n: graph of each vertex
+  int64_t* gbase = nullptr;        // nb+1: first vertex of each graph
+  int64_t* gvol = nullptr;         // nb: vol(V) of each graph
+  uint8_t* gfrozen = nullptr;      // nb: 1 = graph finished, its vertices are not examined
+  int64_t* gcnt = nullptr;         // nb: vertices of the graph that moved or deferred this round
+  std::vector<int64_t> h_gbase;    // host copy of gbase
+
   std::vector<cd_round_trace> trace;
   cd_kernel_profile prof[cd::K_COUNT] = {};
   bool timing = false;
@@ -164,6 +174,7 @@ int check_labels(cd_graph* g, const int32_t* labels_dev);  // CD_EINVAL if out o
 
 // scan.cu
 struct RunOpts {
+  bool batched = false;  // use g's graph partition (per-graph vol, ids, freezing)
   int32_t max_iter;
   int64_t threshold;  // LPA only
   int tie_keep_current, singleton_rule, use_frontier;
@@ -173,6 +184,11 @@ struct RunOpts {
 // Algorithm 1 / Algorithm 2 round loops on g->C (device). Louvain: g->C holds
 // the initial partition; sigma/csize are rebuilt from it.
 int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out);
+// Batched variants (g->nb > 0): per-graph vol(V) and coin ids, frozen graphs
+// skipped. run_lpa_batched freezes a graph after its first round with
+// moved + deferred <= threshold and reports its round count.
+int run_lpa_batched(cd_graph* g, const RunOpts& o, std::vector<int32_t>& rounds);
+void release_batches(cd_graph* g);
 int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves_out,
                    int32_t* rounds_out);
 RunOpts opts_from(const cd_params* p, int32_t level);

@@ -294,7 +294,8 @@ void free_arrays(cd_graph* g) {
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
                 g->hub_mv,       g->hub_build,     g->C,            g->sigma,        g->csize,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
-                g->ctr,          g->status};
+                g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
+                g->gfrozen,      g->gcnt};
   for (void* p : ps) dev_free(p, s);
   if (g->h_ctr) cudaFreeHost(g->h_ctr);
 }

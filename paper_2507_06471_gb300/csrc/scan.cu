@@ -116,13 +116,33 @@ struct ScanCtx {
   int32_t* hub_mv;
   int32_t* hub_build;
   int64_t n_items, nhubs, n_ev_items;
+  // batched mode (gid == nullptr: one graph)
+  const int32_t* gid;
+  const int64_t* gbase;
+  const int64_t* gvol;
+  const uint8_t* gfrozen;
+  unsigned long long* gcnt;
 };
+
+// vol(V) of the graph v belongs to, and v's id inside that graph (the coin
+// uses graph-local ids so that a batched run draws what a solo run draws).
+__device__ __forceinline__ int64_t vol_of(const ScanCtx& s, int32_t v) {
+  return s.gid ? s.gvol[s.gid[v]] : s.vol;
+}
+__device__ __forceinline__ int32_t local_id(const ScanCtx& s, int32_t v) {
+  return s.gid ? v - (int32_t)s.gbase[s.gid[v]] : v;
+}
+// A vertex that wants to change label (moved or deferred) counts toward its
+// graph's stop test.
+__device__ __forceinline__ void count_change(const ScanCtx& s, int32_t v) {
+  if (s.gcnt) atomicAdd(&s.gcnt[s.gid[v]], 1ull);
+}
 
 template <bool LOUV>
 __device__ __forceinline__ typename KeyOf<LOUV>::T cand_key(const ScanCtx& s, int32_t c, int64_t k,
-                                                            int64_t d) {
+                                                            int64_t d, int64_t vol) {
   if constexpr (LOUV)
-    return (i128)s.vol * k - (i128)d * s.sigma[c];
+    return (i128)vol * k - (i128)d * s.sigma[c];
   else
     return k;
 }
@@ -131,14 +151,14 @@ __device__ __forceinline__ typename KeyOf<LOUV>::T cand_key(const ScanCtx& s, in
 template <bool LOUV>
 __device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t cur,
                                           typename KeyOf<LOUV>::T bk, int32_t bc, bool has_cur,
-                                          int64_t kcur) {
+                                          int64_t kcur, int64_t vol) {
   if (bc == NOCAND) return cur;
   if constexpr (!LOUV) {
     if (s.tie_keep && has_cur && kcur == bk) return cur;
     return bc;
   } else {
     int64_t d = s.degw[v];
-    i128 G = bk - (i128)s.vol * kcur + (i128)d * (s.sigma[cur] - d);
+    i128 G = bk - (i128)vol * kcur + (i128)d * (s.sigma[cur] - d);
     if (G <= 0) return cur;  // only strictly positive gains
     if (s.singleton_rule && s.csize[cur] == 1 && s.csize[bc] == 1 && bc > cur) return cur;
     return bc;
@@ -150,7 +170,8 @@ __device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t c
 __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t cur, int32_t target) {
   if (target == cur) return 0;
   if (s.mark) s.flag_nxt[v] = 1;
-  if (commit_coin(s.seed, s.level, s.round, v)) {
+  count_change(s, v);
+  if (commit_coin(s.seed, s.level, s.round, local_id(s, v))) {
     unsigned long long pos = atomicAdd(&s.ctr[C_MOVES], 1ull);
     s.mv_v[pos] = v;
     s.mv_c[pos] = target;
@@ -178,6 +199,7 @@ __device__ __forceinline__ void flush_counters(const ScanCtx& s, int bin, int64_
 }
 
 __device__ __forceinline__ bool is_active(const ScanCtx& s, int32_t v) {
+  if (s.gfrozen && s.gfrozen[s.gid[v]]) return false;
   return s.all_active || s.flag_cur[v];
 }
 
@@ -314,14 +336,16 @@ __global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __re
     int64_t kcur = __shfl_sync(FULL, gsum, cm ? __ffs(cm) - 1 : lane);
     if (!cm) kcur = 0;
     const int64_t dv = (LOUV && act) ? s.degw[v] : 0;
+    const int64_t volv = (LOUV && act) ? vol_of(s, v) : 0;
     const bool ok = leader && (!LOUV || lbl != cur);
-    K bk = ok ? cand_key<LOUV>(s, lbl, gsum, dv) : K(0);
+    K bk = ok ? cand_key<LOUV>(s, lbl, gsum, dv, volv) : K(0);
     int32_t bc = ok ? lbl : NOCAND;
     reduce_best(bk, bc, TILE);
     int32_t target = cur;
-    if (act) target = decide<LOUV>(s, v, cur, bk, bc, cm != 0, kcur);
+    if (act) target = decide<LOUV>(s, v, cur, bk, bc, cm != 0, kcur, volv);
     const bool want = act && target != cur;
-    const bool commit = want && commit_coin(s.seed, s.level, s.round, v);
+    const bool commit = want && commit_coin(s.seed, s.level, s.round, local_id(s, v));
+    if (want && sub == 0) count_change(s, v);
     const unsigned am = __ballot_sync(FULL, commit && sub == 0);
     if (am) {
       const int first = __ffs(am) - 1;
@@ -430,8 +454,8 @@ __device__ __forceinline__ void group_insert(const ScanCtx& s, int32_t v, int64_
 // Read a group's table through its occupied list: every listed slot is a
 // candidate; the slot is cleared for the next vertex.
 template <bool LOUV, class V, int GROUP>
-__device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_t dv, int gl,
-                                           int32_t* keys, V* vals, const uint16_t* occ, int nocc,
+__device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_t dv, int64_t vol,
+                                           int gl, int32_t* keys, V* vals, const uint16_t* occ, int nocc,
                                            typename KeyOf<LOUV>::T& bk, int32_t& bc, bool& hc,
                                            int64_t& kc, int64_t& ncand) {
   for (int j = gl; j < nocc; j += GROUP) {
@@ -446,7 +470,7 @@ __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_
       kc = k;
       if (LOUV) continue;
     }
-    const typename KeyOf<LOUV>::T key = cand_key<LOUV>(s, c, k, dv);
+    const typename KeyOf<LOUV>::T key = cand_key<LOUV>(s, c, k, dv, vol);
     if (better(key, c, bk, bc)) {
       bk = key;
       bc = c;
@@ -493,12 +517,13 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
     group_insert<W, V, GROUP>(s, v, beg, end, gl, keys, vals, occ, &occ_n[gid], lg, stage);
     group_sync<GROUP, NTB>(gid);
     const int64_t dv = LOUV ? s.degw[v] : 0;
+    const int64_t volv = LOUV ? vol_of(s, v) : 0;
     const int nocc = occ_n[gid];
     K bk = K(0);
     int32_t bc = NOCAND;
     bool hc = false;
     int64_t kc = 0;
-    group_eval<LOUV, V, GROUP>(s, cur, dv, gl, keys, vals, occ, nocc, bk, bc, hc, kc, n_cand);
+    group_eval<LOUV, V, GROUP>(s, cur, dv, volv, gl, keys, vals, occ, nocc, bk, bc, hc, kc, n_cand);
     reduce_best(bk, bc, 32);
     unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
@@ -519,7 +544,7 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
       }
     }
     if (gl == 0) {
-      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc);
+      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc, volv);
       const int def = act_single(s, v, cur, target);
       n_def += def;
       ++n_act;
@@ -624,6 +649,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
     if (!is_active(s, v)) continue;  // uniform within the CTA
     const int32_t cur = s.C[v];
     const int64_t dv = LOUV ? s.degw[v] : 0;
+    const int64_t volv = LOUV ? vol_of(s, v) : 0;
     const int64_t base = s.hub_tab[h];
     const int64_t cap = s.hub_tab[h + 1] - base;
     const int64_t e0 = s.hub_ev_slot[it];
@@ -649,7 +675,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
           s.hub_hascur[h] = 1;
           if (LOUV) continue;
         }
-        const K key = cand_key<LOUV>(s, c[j], k[j], dv);
+        const K key = cand_key<LOUV>(s, c[j], k[j], dv, volv);
         if (better(key, c[j], bk, bc)) {
           bk = key;
           bc = c[j];
@@ -692,7 +718,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       }
       const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
       const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
-      const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc);
+      const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc, volv);
       const int def = act_single(s, v, cur, target);
       n_def += def;
       if (target != cur && !def) {
@@ -888,9 +914,19 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
   return CD_OK;
 }
 
-int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out) {
+int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out,
+               std::vector<int32_t>* graph_rounds = nullptr) {
   cudaStream_t st = g->stream;
   const int64_t n = g->n;
+  const bool per_graph_stop = o.batched && graph_rounds != nullptr;
+  std::vector<int64_t> h_gcnt;
+  std::vector<uint8_t> h_frozen;
+  if (per_graph_stop) {
+    graph_rounds->assign(g->nb, o.max_iter);
+    h_gcnt.resize(g->nb);
+    h_frozen.assign(g->nb, 0);
+    CD_CHECK(cudaMemsetAsync(g->gfrozen, 0, g->nb, st));
+  }
   int rc = CD_OK;
   if (g->nhubs > 0) {  // histograms are built from the starting labels in round 0
     const int32_t one = 1;
@@ -908,6 +944,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
   for (int32_t r = 0; r < o.max_iter && rc == CD_OK; ++r) {
     if (g->timing) cudaEventRecord(ev[0], st);
     CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
+    if (per_graph_stop) CD_CHECK(cudaMemsetAsync(g->gcnt, 0, g->nb * sizeof(int64_t), st));
     if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, n, st));
     if (g->nhubs > 0) CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
     ScanCtx s;
@@ -953,6 +990,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.n_items = g->hub_items;
     s.nhubs = g->nhubs;
     s.n_ev_items = g->hub_eval_items;
+    s.gid = o.batched ? g->gid : nullptr;
+    s.gbase = o.batched ? g->gbase : nullptr;
+    s.gvol = o.batched ? g->gvol : nullptr;
+    s.gfrozen = o.batched ? g->gfrozen : nullptr;
+    s.gcnt = per_graph_stop ? (unsigned long long*)g->gcnt : nullptr;
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
     if (louv) {
@@ -973,6 +1015,8 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (rc) break;
     if (g->timing) cudaEventRecord(ev[1], st);
     CD_CHECK(cudaMemcpyAsync(g->h_ctr, g->ctr, C_COUNT * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (per_graph_stop)
+      CD_CHECK(cudaMemcpyAsync(h_gcnt.data(), g->gcnt, g->nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CD_CHECK(cudaStreamSynchronize(st));
     const int64_t* h = g->h_ctr;
     const int64_t moves = h[C_MOVES], deferred = h[C_DEFERRED];
@@ -1027,7 +1071,22 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     total_moves += moves;
     rounds = r + 1;
     std::swap(fcur, fnxt);
-    const bool stop = louv ? (moves + deferred == 0) : (moves + deferred <= o.threshold);
+    bool stop = louv ? (moves + deferred == 0) : (moves + deferred <= o.threshold);
+    if (per_graph_stop) {  // a graph stops after its own round with dN <= threshold
+      bool newly = false, all = true;
+      for (int64_t b = 0; b < g->nb; ++b) {
+        if (h_frozen[b]) continue;
+        if (h_gcnt[b] <= o.threshold) {
+          h_frozen[b] = 1;
+          (*graph_rounds)[b] = r + 1;
+          newly = true;
+        } else {
+          all = false;
+        }
+      }
+      if (newly) CD_CHECK(cudaMemcpyAsync(g->gfrozen, h_frozen.data(), g->nb, cudaMemcpyHostToDevice, st));
+      stop = all;
+    }
     if (stop) break;
   }
   if (g->timing)
@@ -1052,6 +1111,18 @@ int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out) {
                                                                             g->degw, g->n, 0));
   CD_CHECK(cudaGetLastError());
   return run_rounds(g, o, false, nullptr, rounds_out);
+}
+
+int run_lpa_batched(cd_graph* g, const RunOpts& o, std::vector<int32_t>& rounds) {
+  int rc = ensure_run_state(g);
+  if (rc) return rc;
+  if (g->n > 0)
+    CD_LAUNCH(k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, g->stream>>>(g->C, g->sigma, g->csize,
+                                                                                      g->degw, g->n, 0));
+  CD_CHECK(cudaGetLastError());
+  RunOpts ob = o;
+  ob.batched = true;
+  return run_rounds(g, ob, false, nullptr, nullptr, &rounds);
 }
 
 int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves_out,

@@ -263,6 +263,9 @@ def _gpu_lib():
     if _gen_lib is None:
         path = build_gpu_generator()
         L = ctypes.CDLL(path)
+        L.synth_sbm_rows.restype = ctypes.c_int
+        L.synth_sbm_rows.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         L.synth_rmat_keys.restype = ctypes.c_int
         L.synth_rmat_keys.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -393,6 +396,128 @@ def lfr(n: int = 1_000_000, tau1: float = 2.5, dmin: int = 5, dmax: int = 1000,
     g.planted = comm.astype(np.int32)
     g.name = f"lfr_n{n}"
     return g
+
+
+# -------------------------------------------------------------- batches
+
+def pack_batch(graphs) -> "tuple[Graph, np.ndarray]":
+    """Block-diagonal packing of independent graphs: graph b's vertex v
+    becomes vstart[b] + v. Unit weights are materialised as 1 when any graph
+    is weighted. Returns (packed graph, vstart int64[B+1])."""
+    vstart = np.zeros(len(graphs) + 1, dtype=np.int64)
+    astart = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for b, g in enumerate(graphs):
+        vstart[b + 1] = vstart[b] + g.n
+        astart[b + 1] = astart[b] + g.nnz
+    weighted = any(g.w is not None for g in graphs)
+    off = np.zeros(vstart[-1] + 1, dtype=np.int64)
+    cols = np.zeros(astart[-1], dtype=np.int32)
+    w = np.ones(astart[-1], dtype=np.int32) if weighted else None
+    for b, g in enumerate(graphs):
+        go = g.off.cpu().numpy()
+        off[vstart[b] + 1: vstart[b + 1] + 1] = go[1:] + astart[b]
+        cols[astart[b]: astart[b + 1]] = g.cols.cpu().numpy() + vstart[b]
+        if weighted and g.w is not None:
+            w[astart[b]: astart[b + 1]] = g.w.cpu().numpy()
+    packed = Graph(int(vstart[-1]), torch.from_numpy(off), torch.from_numpy(cols),
+                   None if w is None else torch.from_numpy(w))
+    packed.name = f"batch{len(graphs)}"
+    return packed, vstart
+
+
+def batch_specs(count: int = 4096, seed: int = 4, nmin: int = 50, nmax: int = 5000,
+                kmin: int = 2, kmax: int = 50):
+    """Seeded recipe of a batch: per graph (n log-uniform in [nmin, nmax],
+    k uniform in {kmin..kmax}, seed + b)."""
+    key = stream_key(seed, TAG_SBM ^ 0xBA7C4)
+    r = draw(key, np.arange(2 * count, dtype=np.uint64))
+    u = (r[:count] >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    ns = np.floor(np.exp(np.log(nmin) + u * (np.log(nmax + 1) - np.log(nmin)))).astype(np.int64)
+    ns = np.clip(ns, nmin, nmax)
+    ks = uniform_int(r[count:], kmin, kmax)
+    ks = np.minimum(ks, ns)
+    return [(int(n), int(k), seed + b) for b, (n, k) in enumerate(zip(ns, ks))]
+
+
+def sbm_batch_device(specs, p_in="0.2", p_out="0.002", wmax: int = 4, device: str = "cuda"):
+    """The planted-partition graphs of `specs` [(n, k, seed), ...] generated on
+    the device with the same definition as `sbm` (identical edges, the same
+    seeded relabelling and weights), packed block-diagonally.
+    Returns (packed Graph on `device`, vstart int64[B+1], planted int32[n])."""
+    B = len(specs)
+    ns = np.array([n for n, _, _ in specs], dtype=np.int64)
+    vstart = np.zeros(B + 1, dtype=np.int64)
+    vstart[1:] = np.cumsum(ns)
+    rows = int(vstart[-1])
+    row_graph = np.repeat(np.arange(B, dtype=np.int32), ns)
+    blocks = np.array([k for _, k, _ in specs], dtype=np.int32)
+    keys = np.array([stream_key(sd, TAG_SBM) for _, _, sd in specs], dtype=np.uint64)
+    t_in, t_out = threshold64(p_in), threshold64(p_out)
+    pin = float(Fraction(str(p_in)))
+    pairs = float(sum(n * (n - 1) // 2 for n in ns))
+    cap = int(pairs * max(pin, float(Fraction(str(p_out)))) * 1.2) + 1024
+    d = lambda a: torch.from_numpy(a).to(device)
+    t_vstart, t_rg, t_blocks, t_keys = d(vstart), d(row_graph), d(blocks), d(keys.view(np.int64))
+    out = torch.empty(cap, dtype=torch.int64, device=device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=device)
+    stream = torch.cuda.current_stream(out.device).cuda_stream
+    rc = _gpu_lib().synth_sbm_rows(t_vstart.data_ptr(), t_rg.data_ptr(), t_blocks.data_ptr(), t_keys.data_ptr(),
+                                   t_in, t_out, rows, out.data_ptr(), cnt.data_ptr(), cap, stream)
+    if rc != 0:
+        raise RuntimeError("synth_sbm_rows failed")
+    m = int(cnt.item())
+    if m > cap:
+        raise RuntimeError("SBM edge buffer too small")
+    e = out[:m]
+    b = e >> 40
+    u = (e >> 20) & 0xFFFFF
+    v = e & 0xFFFFF
+    # the per-graph seeded relabelling of `sbm`: new id of old vertex x
+    inv = np.empty(rows, dtype=np.int64)
+    planted = np.empty(rows, dtype=np.int32)
+    for gi, (n, k, sd) in enumerate(specs):
+        p = permutation(n, sd)
+        loc = np.empty(n, dtype=np.int64)
+        loc[p] = np.arange(n)
+        inv[vstart[gi]:vstart[gi + 1]] = loc
+        bsz = max(n // k, 1)
+        planted[vstart[gi]:vstart[gi + 1]] = np.minimum(np.arange(n) // bsz, k - 1)[p]
+    t_inv = d(inv)
+    base = t_vstart[b]
+    nu = t_inv[base + u]
+    nv = t_inv[base + v]
+    lo = torch.minimum(nu, nv)
+    hi = torch.maximum(nu, nv)
+    local = torch.unique(b * (1 << 40) + lo * (1 << 20) + hi, sorted=True)
+    b = local >> 40
+    lo = (local >> 20) & 0xFFFFF
+    hi = local & 0xFFFFF
+    gkeys = (t_vstart[b] + lo) * (1 << 32) + (t_vstart[b] + hi)
+    w = None
+    if wmax > 1:
+        wkeys = np.array([stream_key(sd, TAG_W) for _, _, sd in specs], dtype=np.uint64)
+        bk = wkeys[b.cpu().numpy()]
+        ctr = (lo * (1 << 32) + hi).cpu().numpy().astype(np.uint64)
+        with np.errstate(over="ignore"):
+            z = bk + (ctr + np.uint64(1)) * np.uint64(GAMMA)
+        w = torch.from_numpy(uniform_int(mix64(z), 1, wmax).astype(np.int32)).to(device)
+    g = csr_from_edge_keys(gkeys, rows, w)
+    g.planted = planted
+    g.name = f"sbm_batch{B}"
+    return g, vstart, planted
+
+
+def unpack_batch(packed: Graph, vstart) -> "list[Graph]":
+    """The member graphs of a block-diagonal batch, with local vertex ids."""
+    out = []
+    off = packed.off
+    for b in range(len(vstart) - 1):
+        a0, a1 = int(off[vstart[b]]), int(off[vstart[b + 1]])
+        o = off[vstart[b]:vstart[b + 1] + 1] - a0
+        c = packed.cols[a0:a1] - int(vstart[b])
+        w = None if packed.w is None else packed.w[a0:a1]
+        out.append(Graph(int(vstart[b + 1] - vstart[b]), o, c.to(torch.int32), w))
+    return out
 
 
 # -------------------------------------------------------------- small helpers

@@ -37,7 +37,48 @@ __global__ void rmat_keys_kernel(uint64_t key, int scale, uint32_t tA, uint32_t 
   }
 }
 
+// Planted-partition pairs of many graphs: thread per row u of graph b; the
+// pair {u, v} (u < v, ids local to b) is an edge iff draw number u * n_b + v
+// of graph b's stream is below the threshold for "same block" (p_in) or
+// "different blocks" (p_out); block(u) = min(u / (n_b / k_b), k_b - 1).
+// Edges are appended as (b << 40 | u << 20 | v).
+__global__ void sbm_rows_kernel(const int64_t* __restrict__ vstart, const int32_t* __restrict__ row_graph,
+                                const int32_t* __restrict__ blocks, const uint64_t* __restrict__ keys,
+                                uint64_t t_in, uint64_t t_out, int64_t rows, int64_t* __restrict__ out,
+                                unsigned long long* __restrict__ out_n, int64_t cap) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += stride) {
+    const int32_t b = row_graph[r];
+    const int64_t n = vstart[b + 1] - vstart[b];
+    const int64_t u = r - vstart[b];
+    const int64_t k = blocks[b];
+    int64_t bsz = n / k;
+    if (bsz < 1) bsz = 1;
+    const int64_t bu = u / bsz < k - 1 ? u / bsz : k - 1;
+    for (int64_t v = u + 1; v < n; ++v) {
+      const int64_t bv = v / bsz < k - 1 ? v / bsz : k - 1;
+      const uint64_t x = sm64_draw(keys[b], (uint64_t)(u * n + v));
+      if (x < (bu == bv ? t_in : t_out)) {
+        const unsigned long long pos = atomicAdd(out_n, 1ull);
+        if ((int64_t)pos < cap) out[pos] = ((int64_t)b << 40) | (u << 20) | v;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+extern "C" int synth_sbm_rows(const void* vstart, const void* row_graph, const void* blocks, const void* keys,
+                              uint64_t t_in, uint64_t t_out, int64_t rows, void* out, void* out_n, int64_t cap,
+                              void* stream) {
+  if (rows <= 0) return 0;
+  int64_t nb = (rows + 255) / 256;
+  if (nb > 152 * 64) nb = 152 * 64;
+  sbm_rows_kernel<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(
+      (const int64_t*)vstart, (const int32_t*)row_graph, (const int32_t*)blocks, (const uint64_t*)keys, t_in,
+      t_out, rows, (int64_t*)out, (unsigned long long*)out_n, cap);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
 
 extern "C" int synth_rmat_keys(uint64_t key, int scale, uint32_t tA, uint32_t tAB, uint32_t tABC,
                                int64_t first, int64_t count, void* out, void* stream) {
