@@ -41,6 +41,8 @@ WORKLOADS = {
     "lfr1m": "LFR-style n = 1,000,000, degree power law 2.5 on [5,1000], community sizes 1.5 on "
              "[20,5000], mu = 0.3, weights U{1..8}, seed 2",
     "sbm10k": "planted-partition SBM n = 10,000, 100 blocks, p_in = 0.1, p_out = 0.001, seed 1",
+    "batch4096": "4,096 planted-partition SBM graphs, n log-uniform in [50, 5000], k uniform in {2..50}, "
+                 "p_in = 0.2, p_out = 0.002, weights U{1..4}, seeds 4+b, packed block-diagonally",
 }
 
 
@@ -56,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--solo-sample", type=int, default=128,
+                    help="batch workload: graphs timed one call per graph for the comparison")
     return ap.parse_args()
 
 
@@ -273,6 +277,112 @@ def run_reference(args, rank, world):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------------------ batched workload
+
+def run_batch(args, rank, world, local):
+    """Louvain on 4,096 graphs at once (batched mode) vs one call per graph."""
+    import numpy as np
+    import torch
+
+    import paper_2507_06471_gb300 as cd
+    import synth
+
+    cd.lib()
+    specs = synth.batch_specs(4096, seed=4 + 4096 * rank)
+    g, vstart, _ = synth.sbm_batch_device(specs)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    B = len(specs)
+    lab = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    params = cd.cd_params_default()
+    stream = torch.cuda.current_stream()
+
+    # autotune the degree bins once on this workload (untimed)
+    h = cd.cd_csr_upload(g.off, g.cols, g.w)
+    tw, th = cd.cd_autotune(h, cd.cd_params_default(), 3)
+    cd.cd_graph_free(h)
+
+    def step(timing=False):
+        params.timing = 1 if timing else 0
+        h = cd.cd_csr_upload(g.off, g.cols, g.w)
+        cd.cd_graph_set_bins(h, tw, th)
+        cd.cd_graph_set_batches(h, vstart)
+        levels, q = cd.cd_batch_louvain_run(h, params, lab, B)
+        tr = cd.cd_trace_get(h)
+        prof = cd.cd_profile_get(h) if timing else []
+        cd.cd_graph_free(h)
+        return sum(t["arcs"] for t in tr), len(tr), levels, q, prof
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = cd.cd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    arcs = 0
+    prof = {}
+    for _ in range(args.steps):
+        a, rounds, levels, q, p = step(timing=True)
+        arcs += a
+        merge_profiles(prof, p)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = cd.cd_launch_count() - launches0
+    clk = clocks.stop()
+    ms = allreduce_max(ev0.elapsed_time(ev1), world)
+    graphs_per_s = allreduce_sum(float(B * args.steps), world) / (ms / 1e3)
+
+    # one call per graph (upload + cd_louvain_run) on an evenly spaced sample
+    members = synth.unpack_batch(g, vstart)
+    pick = np.linspace(0, B - 1, min(args.solo_sample, B)).astype(int)
+    solo_lab = [torch.empty(members[b].n, dtype=torch.int32, device="cuda") for b in pick]
+    same = True
+    lab_h = lab.cpu().numpy()
+    for i, b in enumerate(pick[:8]):  # warm-up of the solo path
+        m = members[b]
+        h = cd.cd_csr_upload(m.off, m.cols, m.w)
+        cd.cd_louvain_run(h, cd.cd_params_default(), solo_lab[i])
+        cd.cd_graph_free(h)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, b in enumerate(pick):
+        m = members[b]
+        h = cd.cd_csr_upload(m.off, m.cols, m.w)
+        cd.cd_louvain_run(h, cd.cd_params_default(), solo_lab[i])
+        cd.cd_graph_free(h)
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    for i, b in enumerate(pick):
+        same = same and bool(np.array_equal(solo_lab[i].cpu().numpy(), lab_h[vstart[b]:vstart[b + 1]]))
+    solo_gps = len(pick) / solo_s
+    total_prof_ms = sum(v["total_ms"] for v in prof.values())
+    kernels = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
+                   "share": round(v["total_ms"] / total_prof_ms, 4) if total_prof_ms else 0}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]) if v["launches"]}
+    line = {"metric": "batched graphs/s (Louvain to convergence, all graphs in one call)",
+            "value": graphs_per_s, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "batch4096", "description": WORKLOADS["batch4096"], "graphs": B,
+                       "n": g.n, "arcs": g.nnz, "parallelism": f"replicas x{world}",
+                       "bins_autotuned": {"t_warp": tw, "t_hub": th}},
+            "gteps": arcs / (ms / 1e3) / 1e9 * world, "louvain_rounds": rounds,
+            "max_levels_reached": int(levels.max()), "mean_q": float(np.mean(q)),
+            "solo": {"graphs_per_s": solo_gps, "sample": int(len(pick)), "same_labels_as_batched": same,
+                     "how": "cd_csr_upload + cd_louvain_run per graph, one graph at a time"},
+            "speedup_vs_solo": graphs_per_s / solo_gps, "kernels": kernels, "gpu_launches": launches,
+            "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
+
+
 # ------------------------------------------------------------------ main
 
 def main():
@@ -280,6 +390,9 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch4096":
+        run_batch(args, rank, world, local)
         return
     import numpy as np
     import torch

@@ -173,6 +173,19 @@ int cd_batch_lpa_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int o
 int cd_batch_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
                          int32_t* levels_out, double* q_out);
 
+/* Degree bins (performance only; results never depend on them): vertices of
+ * degree 33..t_warp are scanned by one warp, t_warp+1..t_hub by 128 threads
+ * with a shared-memory table, and vertices above t_hub keep persistent label
+ * histograms updated by their neighbours' moves. 32 <= t_warp <= 256,
+ * t_warp <= t_hub <= 1024; defaults 256 and 1024. */
+int cd_graph_set_bins(cd_graph* g, int32_t t_warp, int32_t t_hub);
+
+/* Autotuner: time `rounds` rounds of LPA plus `rounds` rounds of local moving
+ * for every candidate (t_warp in {64,128,256}) x (t_hub in {256,512,1024}),
+ * keep the fastest bins on g (coarse Louvain levels inherit them) and report
+ * them (outputs may be NULL). */
+int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp_out, int32_t* t_hub_out);
+
 /* Copy up to cap per-round records of the last run on g into out; *count
  * receives the number of records available. */
 int cd_trace_get(const cd_graph* g, cd_round_trace* out, int32_t cap, int32_t* count);

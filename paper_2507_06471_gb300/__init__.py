@@ -28,7 +28,7 @@ EXPORTED = [
     "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
     "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
     "cd_launch_count", "cd_modularity_noalloc", "cd_graph_set_batches", "cd_batch_lpa_run",
-    "cd_batch_louvain_run",
+    "cd_batch_louvain_run", "cd_graph_set_bins", "cd_autotune",
 ]
 
 
@@ -88,6 +88,8 @@ def lib():
         L.cd_launch_count.argtypes = []
         L.cd_modularity_noalloc.argtypes = [_P, _P, _P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P]
         L.cd_graph_set_batches.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int]
+        L.cd_graph_set_bins.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+        L.cd_autotune.argtypes = [_P, ctypes.POINTER(cd_params), ctypes.c_int32, _P, _P]
         L.cd_batch_lpa_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P]
         L.cd_batch_louvain_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P, _P]
         _lib = L
@@ -259,6 +261,16 @@ def cd_batch_louvain_run(g, params: cd_params, labels_out, n_graphs: int):
     _check(lib().cd_batch_louvain_run(g, ctypes.byref(params), p, dev, _ptr(levels)[0], _ptr(q)[0]),
            "cd_batch_louvain_run")
     return levels, q
+
+
+def cd_graph_set_bins(g, t_warp: int, t_hub: int) -> None:
+    _check(lib().cd_graph_set_bins(g, t_warp, t_hub), "cd_graph_set_bins")
+
+
+def cd_autotune(g, params: cd_params, rounds: int = 3):
+    tw, th = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().cd_autotune(g, ctypes.byref(params), rounds, ctypes.byref(tw), ctypes.byref(th)), "cd_autotune")
+    return tw.value, th.value
 
 
 def cd_launch_count() -> int:

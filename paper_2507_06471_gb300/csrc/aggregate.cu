@@ -278,7 +278,7 @@ int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, 
     return rc;
   }
   cd_graph* c = nullptr;
-  rc = graph_adopt(s, k, nseg, coff, ccols, cw, W_I64, &c);
+  rc = graph_adopt(s, k, nseg, coff, ccols, cw, W_I64, &c, nullptr, nullptr, g);
   if (rc) return rc;
   c->timing = g->timing;
   *coarse_out = c;

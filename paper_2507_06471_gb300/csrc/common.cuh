@@ -22,6 +22,8 @@ enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_HUB, NBINS };
 constexpr int WARP_MAX = 256;    // a warp per vertex, table <= 512 slots
 constexpr int BLK1_MAX = 1024;   // 128 threads per vertex, table <= 2048 slots
 constexpr int BLOCK_MAX = 1024;  // largest degree scanned through shared-memory tables
+// The runtime bin boundaries t_warp (warp vs 128-thread group) and t_hub
+// (group vs hub histogram) may be lowered below these capacities (autotuner).
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
 constexpr int HUB_SLICE = 4096;  // histogram slots per hub evaluate item
 constexpr int COL_PAD = 4;       // column arrays carry 4 spare entries for 16-byte loads
@@ -100,6 +102,8 @@ struct cd_graph {
   int32_t* hub_mv = nullptr;               // 3 x nhubs: moved flag, old label, new label
   int32_t* hub_build = nullptr;            // 1: tables must be rebuilt before the next scan
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
+  int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
+  int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads; above: hub
 
   // run state (allocated on first use)
   int32_t* C = nullptr;
@@ -168,8 +172,10 @@ int profile_flush(cd_graph* g);  // syncs, accumulates pending events
 // Takes ownership of device arrays in the internal convention (loop arcs 2L).
 int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* cols, void* w,
                 int wkind, cd_graph** out, int64_t* degw_pre = nullptr,
-                const unsigned long long* stats_pre = nullptr);
+                const unsigned long long* stats_pre = nullptr, const cd_graph* like = nullptr);
 int ensure_run_state(cd_graph* g);
+// Recompute the degree bins and hub structures for new boundaries.
+int rebin(cd_graph* g, int t_warp, int t_hub);
 int check_labels(cd_graph* g, const int32_t* labels_dev);  // CD_EINVAL if out of [0, n)
 
 // scan.cu

@@ -106,14 +106,28 @@ constexpr int NSTATS = 4 + NBINS;
 
 __device__ __forceinline__ void fail(int32_t* status, int code) { atomicCAS(status, 0, code); }
 
-__device__ __forceinline__ int bin_of(int64_t d) {
+__device__ __forceinline__ int bin_of(int64_t d, int t_warp = WARP_MAX, int t_hub = BLOCK_MAX) {
   if (d <= 4) return B_T4;
   if (d <= 8) return B_T8;
   if (d <= 16) return B_T16;
   if (d <= 32) return B_T32;
-  if (d <= WARP_MAX) return B_WARP;
-  if (d <= BLK1_MAX) return B_BLK1;
+  if (d <= t_warp) return B_WARP;
+  if (d <= t_hub) return B_BLK1;
   return B_HUB;
+}
+
+__global__ void k_bin_count(const int64_t* __restrict__ off, int64_t n, int t_warp, int t_hub,
+                            unsigned long long* counts) {
+  __shared__ unsigned long long sb[NBINS];
+  if (threadIdx.x < NBINS) sb[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const int64_t d = off[v + 1] - off[v];
+    if (d > 0) atomicAdd(&sb[bin_of(d, t_warp, t_hub)], 1ull);
+  }
+  __syncthreads();
+  if (threadIdx.x < NBINS && sb[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sb[threadIdx.x]);
 }
 
 template <class OffT>
@@ -205,8 +219,8 @@ __global__ void __launch_bounds__(NT) k_double_loops(const int64_t* __restrict__
     }
 }
 
-__global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off, int64_t n,
-                                                 const int64_t* __restrict__ bin_base,
+__global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off, int64_t n, int t_warp,
+                                                 int t_hub, const int64_t* __restrict__ bin_base,
                                                  unsigned long long* cursor,
                                                  int32_t* __restrict__ list) {
   const int lane = threadIdx.x & 31;
@@ -217,7 +231,7 @@ __global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off
     int b = -1;
     if (v < n) {
       int64_t d = off[v + 1] - off[v];
-      if (d > 0) b = bin_of(d);
+      if (d > 0) b = bin_of(d, t_warp, t_hub);
     }
 #pragma unroll
     for (int bb = 0; bb < NBINS; ++bb) {
@@ -300,18 +314,63 @@ void free_arrays(cd_graph* g) {
   if (g->h_ctr) cudaFreeHost(g->h_ctr);
 }
 
-// Bins, hub tables and status word of a graph whose CSR, weights and deg_w
+void free_bins(cd_graph* g) {
+  cudaStream_t s = g->stream;
+  void* ps[] = {g->bin_list,     g->hub_idx,     g->hub_bits,     g->hub_tab,   g->hub_slot,
+                g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
+                g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
+                g->hub_build};
+  for (void* p : ps) dev_free(p, s);
+  g->bin_list = nullptr;
+  g->hub_idx = nullptr;
+  g->hub_bits = nullptr;
+  g->hub_tab = nullptr;
+  g->hub_slot = nullptr;
+  g->hub_item_hub = nullptr;
+  g->hub_item_arc = nullptr;
+  g->hub_ev_hub = nullptr;
+  g->hub_ev_slot = nullptr;
+  g->hub_ev_first = nullptr;
+  g->hub_part = nullptr;
+  g->hub_cur = nullptr;
+  g->hub_hascur = nullptr;
+  g->hub_done = nullptr;
+  g->hub_mv = nullptr;
+  g->hub_build = nullptr;
+  g->nhubs = g->hub_slots = g->hub_items = g->hub_eval_items = 0;
+}
+
+int build_bins(cd_graph* g);
+
+// Scalars, bins and hub structures of a graph whose CSR, weights and deg_w
 // are in place; stats from k_ingest.
 int finish_graph(cd_graph* g, const unsigned long long* stats) {
-  cudaStream_t s = g->stream;
   g->vol = (int64_t)stats[0];
   g->n_isolated = (int64_t)stats[2];
   g->max_degw = (int64_t)stats[3];
   if (stats[0] >= (1ull << 62)) return CD_EOVERFLOW;
-  g->bin_start[0] = 0;
-  for (int b = 0; b < NBINS; ++b) g->bin_start[b + 1] = g->bin_start[b] + (int64_t)stats[4 + b];
+  return build_bins(g);
+}
+
+// Degree bins for (t_warp, t_hub), and the hub histograms' layout.
+int build_bins(cd_graph* g) {
+  cudaStream_t s = g->stream;
+  int rc;
+  {
+    unsigned long long* d_cnt = nullptr;
+    unsigned long long h_cnt[NBINS] = {};
+    if ((rc = dev_alloc_t(&d_cnt, NBINS, s))) return rc;
+    CD_CHECK(cudaMemsetAsync(d_cnt, 0, NBINS * sizeof(unsigned long long), s));
+    if (g->n > 0)
+      CD_LAUNCH(k_bin_count<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, g->t_warp, g->t_hub, d_cnt));
+    CD_CHECK(cudaMemcpyAsync(h_cnt, d_cnt, sizeof(h_cnt), cudaMemcpyDeviceToHost, s));
+    CD_CHECK(cudaStreamSynchronize(s));
+    dev_free(d_cnt, s);
+    g->bin_start[0] = 0;
+    for (int b = 0; b < NBINS; ++b) g->bin_start[b + 1] = g->bin_start[b] + (int64_t)h_cnt[b];
+  }
   int64_t listed = g->bin_start[NBINS];
-  int rc = dev_alloc_t(&g->bin_list, listed, s);
+  rc = dev_alloc_t(&g->bin_list, listed, s);
   if (rc) return rc;
   int64_t* d_base = nullptr;
   unsigned long long* d_cur = nullptr;
@@ -319,7 +378,9 @@ int finish_graph(cd_graph* g, const unsigned long long* stats) {
   if ((rc = dev_alloc_t(&d_cur, NBINS, s))) return rc;
   CD_CHECK(cudaMemcpyAsync(d_base, g->bin_start, NBINS * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CD_CHECK(cudaMemsetAsync(d_cur, 0, NBINS * sizeof(unsigned long long), s));
-  if (g->n > 0) CD_LAUNCH(k_bin_fill<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, d_base, d_cur, g->bin_list));
+  if (g->n > 0)
+    CD_LAUNCH(k_bin_fill<<<grid_for(g->n), NT, 0, s>>>(g->off, g->n, g->t_warp, g->t_hub, d_base, d_cur,
+                                                       g->bin_list));
   CD_CHECK(cudaGetLastError());
   // hubs: host-side layout of tables and work items
   int64_t nh = g->bin_start[B_HUB + 1] - g->bin_start[B_HUB];
@@ -421,6 +482,16 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
 
 }  // namespace
 
+int rebin(cd_graph* g, int t_warp, int t_hub) {
+  if (t_warp < 32 || t_warp > WARP_MAX || t_hub < t_warp || t_hub > BLOCK_MAX) return CD_EINVAL;
+  if (t_warp == g->t_warp && t_hub == g->t_hub && g->bin_list) return CD_OK;
+  CD_CHECK(cudaStreamSynchronize(g->stream));
+  free_bins(g);
+  g->t_warp = t_warp;
+  g->t_hub = t_hub;
+  return build_bins(g);
+}
+
 int ensure_run_state(cd_graph* g) {
   if (g->C) return CD_OK;
   cudaStream_t s = g->stream;
@@ -450,8 +521,13 @@ int check_labels(cd_graph* g, const int32_t* labels_dev) {
 // arcs carry 2L). If degw_pre is given (with its ingest stats) it is adopted
 // too; otherwise deg_w is computed as the plain row sum.
 int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* cols, void* w,
-                int wkind, cd_graph** out, int64_t* degw_pre, const unsigned long long* stats_pre) {
+                int wkind, cd_graph** out, int64_t* degw_pre, const unsigned long long* stats_pre,
+                const cd_graph* like) {
   cd_graph* g = new cd_graph();
+  if (like) {
+    g->t_warp = like->t_warp;
+    g->t_hub = like->t_hub;
+  }
   g->stream = s;
   g->n = n;
   g->nnz = nnz;

@@ -1207,4 +1207,53 @@ int cd_louvain_local_move(cd_graph* g, const cd_params* p, int32_t* labels_io, i
   return CD_OK;
 }
 
+int cd_graph_set_bins(cd_graph* g, int32_t t_warp, int32_t t_hub) {
+  if (!g) return CD_EINVAL;
+  return rebin(g, t_warp, t_hub);
+}
+
+int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp_out, int32_t* t_hub_out) {
+  if (!g || !p || rounds < 1) return CD_EINVAL;
+  static const int tw[] = {64, 128, 256};
+  static const int th[] = {256, 512, 1024};
+  int rc = ensure_run_state(g);
+  if (rc) return rc;
+  cudaEvent_t a, b;
+  CD_CHECK(cudaEventCreate(&a));
+  CD_CHECK(cudaEventCreate(&b));
+  float best = -1.f;
+  int bw = g->t_warp, bh = g->t_hub;
+  const bool timing = g->timing;
+  g->timing = false;
+  for (int i = 0; i < 3 && !rc; ++i)
+    for (int j = 0; j < 3 && !rc; ++j) {
+      if (th[j] < tw[i]) continue;
+      if ((rc = rebin(g, tw[i], th[j]))) break;
+      RunOpts o = opts_from(p, 0);
+      o.max_iter = rounds;
+      cudaEventRecord(a, g->stream);
+      rc = run_lpa(g, o, nullptr);
+      if (!rc) rc = run_local_move(g, o, 0, nullptr, nullptr);
+      cudaEventRecord(b, g->stream);
+      if (rc) break;
+      cudaEventSynchronize(b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (best < 0.f || ms < best) {
+        best = ms;
+        bw = tw[i];
+        bh = th[j];
+      }
+    }
+  g->timing = timing;
+  g->trace.clear();
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if ((rc = rebin(g, bw, bh))) return rc;
+  if (t_warp_out) *t_warp_out = bw;
+  if (t_hub_out) *t_hub_out = bh;
+  return CD_OK;
+}
+
 }  // extern "C"

@@ -110,3 +110,13 @@ def test_batches_must_not_share_arcs():
     G.set_batches(np.array([0, 2, 5, 6], dtype=np.int64))
     lab, levels, q = G.batch_louvain()
     assert lab.shape == (6,)
+
+
+def test_device_batch_generator_matches_host_sbm():
+    specs = [(300, 5, 11), (57, 2, 12), (1000, 40, 13), (2, 2, 14)]
+    packed, vstart, planted = synth.sbm_batch_device(specs)
+    members = synth.unpack_batch(packed.to("cpu"), vstart)
+    for (n, k, sd), m in zip(specs, members):
+        h = synth.sbm(n, k, "0.2", "0.002", seed=sd, wmax=4)
+        assert torch.equal(m.off, h.off) and torch.equal(m.cols, h.cols) and torch.equal(m.w, h.w)
+    assert np.array_equal(planted[vstart[0]:vstart[1]], synth.sbm(300, 5, "0.2", "0.002", seed=11).planted)
