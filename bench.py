@@ -43,6 +43,9 @@ WORKLOADS = {
     "sbm10k": "planted-partition SBM n = 10,000, 100 blocks, p_in = 0.1, p_out = 0.001, seed 1",
     "batch4096": "4,096 planted-partition SBM graphs, n log-uniform in [50, 5000], k uniform in {2..50}, "
                  "p_in = 0.2, p_out = 0.002, weights U{1..4}, seeds 4+b, packed block-diagonally",
+    "serve2048": "stream of 2,048 requests (1/3 LPA, 2/3 Louvain, seeded): 1,984 planted-partition SBM "
+                 "graphs as in batch4096, 48 SBM graphs with n log-uniform in [10,000, 30,000] and "
+                 "blocks of 100, 16 R-MAT graphs of scale 14-17 (edge factor 16); host buffers",
 }
 
 
@@ -58,6 +61,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--solo-sample", type=int, default=128,
                     help="batch workload: graphs timed one call per graph for the comparison")
     return ap.parse_args()
@@ -253,6 +257,9 @@ def run_reference(args, rank, world):
     """The oracle on the host cores, timed on bounded samples of the workload."""
     if rank != 0:
         return
+    if args.workload in ("batch4096", "serve2048"):
+        run_reference_many(args)
+        return
     import torch
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     g, scale = make_graph(args.workload, args.scale, dev)
@@ -275,6 +282,188 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_reference_many(args, budget_s: float = 20.0):
+    """The oracle solving the graphs of a many-graph workload one after another
+    (in their order, until a time budget per step is spent)."""
+    import numpy as np
+    import oracle
+    if args.workload == "batch4096":
+        import synth
+        reqs = [(2, *host_graph(synth.sbm(n, k, "0.2", "0.002", seed=sd, wmax=4)))
+                for n, k, sd in synth.batch_specs(4096, seed=4)[:64]]
+    else:
+        reqs = [(k, o, c, None if w is None else w.astype(np.int64)) for k, o, c, w in serve_requests(11)]
+    per_step = max(1.0, budget_s / max(1, args.steps + args.warmup))
+    done, secs, i = 0, 0.0, 0
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        cnt = 0
+        while time.perf_counter() - t0 < per_step:
+            kind, off, cols, w = reqs[i % len(reqs)]
+            i += 1
+            if kind == 1:
+                oracle.lpa(off, cols, w)
+            else:
+                oracle.louvain(off, cols, w)
+            cnt += 1
+        if step >= args.warmup:
+            done += cnt
+            secs += time.perf_counter() - t0
+    unit = "graphs/s" if args.workload == "batch4096" else "requests/s"
+    value = done / secs
+    sample = f"oracle (plain C, 1 thread) solving the workload's graphs one by one, {done} graphs in {secs:.1f} s"
+    line = {"impl": "reference", "metric": unit, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload, "description": WORKLOADS[args.workload]},
+            "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ serving workload
+
+def serve_requests(seed: int):
+    """The serve2048 request stream as host arrays: [(kind, off int64, cols int32, w int32|None)]."""
+    import numpy as np
+    import torch
+
+    import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    rng = np.random.default_rng(seed)
+    small = synth.batch_specs(1984, seed=seed)
+    mid_n = np.exp(rng.uniform(np.log(10_000), np.log(30_000), 48)).astype(np.int64)
+    mid = [(int(n), int(n) // 100, seed * 1000 + j) for j, n in enumerate(mid_n)]
+    graphs = []
+    for part in (small, mid):
+        if dev == "cuda":
+            g, vstart, _ = synth.sbm_batch_device(part)
+            graphs += synth.unpack_batch(g.to("cpu"), vstart)
+        else:
+            graphs += [synth.sbm(n, k, "0.2", "0.002", seed=sd, wmax=4) for n, k, sd in part]
+    for j in range(16):
+        graphs.append(synth.rmat(14 + j % 4, 16, seed=seed * 100 + j, device=dev).to("cpu"))
+    order = rng.permutation(len(graphs))
+    kinds = rng.integers(0, 3, len(graphs))
+    out = []
+    for i, o in enumerate(order):
+        g = graphs[o]
+        off = g.off.numpy().astype(np.int64)
+        cols = g.cols.numpy().astype(np.int32)
+        w = None if g.w is None else g.w.numpy().astype(np.int32)
+        out.append((1 if kinds[i] == 0 else 2, off, cols, w))
+    return out
+
+
+def run_serve(args, rank, world, local):
+    """Requests through the serving engine (continuous batching over worker
+    streams) vs the same requests one call at a time."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2507_06471_gb300 as cd
+
+    cd.lib()
+    reqs = serve_requests(11 + 7919 * rank)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    R = len(reqs)
+    h2d = sum(o.nbytes + c.nbytes + (0 if w is None else w.nbytes) for _, o, c, w in reqs)
+    d2h = sum(4 * (len(o) - 1) for _, o, _, _ in reqs)
+
+    def burst(srv, subset=None):
+        rs = reqs if subset is None else [reqs[i] for i in subset]
+        t0 = time.perf_counter()
+        ids = [srv.submit(k, o, c, w) for k, o, c, w in rs]
+        out = [srv.result(i) for i in ids]
+        return time.perf_counter() - t0, out
+
+    srv = cd.Server(slots=args.serve_slots, small_n=8192, batch_arcs=1 << 22)
+    for _ in range(args.warmup):
+        burst(srv)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = cd.cd_launch_count()
+    secs, lat, queue, packed = [], [], [], []
+    last = None
+    for _ in range(args.steps):
+        dt, last = burst(srv)
+        secs.append(dt)
+        lat += [r.latency_ms for _, r in last]
+        queue += [r.queue_ms for _, r in last]
+        packed += [r.batched_with for _, r in last]
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = cd.cd_launch_count() - launches0
+    clk = clocks.stop()
+    wall = allreduce_max(sum(secs), world)
+    value = allreduce_sum(float(R * args.steps), world) / wall
+    stats = srv.stats()
+
+    # open loop: Poisson arrivals at half the measured throughput of this rank
+    rate = 0.5 * R * args.steps / sum(secs)
+    gaps = np.random.default_rng(5).exponential(1.0 / rate, R)
+    ids = []
+
+    def feed():
+        t = time.perf_counter()
+        for i, (k, o, c, w) in enumerate(reqs):
+            t += gaps[i]
+            d = t - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            ids.append(srv.submit(k, o, c, w))
+
+    th = threading.Thread(target=feed)
+    th.start()
+    th.join()
+    ol = [srv.result(i)[1] for i in ids]
+    srv.close()
+
+    # one call at a time (no packing, one worker) on an evenly spaced sample
+    pick = np.linspace(0, R - 1, min(256, R)).astype(int)
+    solo = cd.Server(slots=1, small_n=0)
+    burst(solo, pick[:8])
+    solo_s, solo_out = burst(solo, pick)
+    solo.close()
+    same = all(np.array_equal(solo_out[j][0], last[i][0]) and solo_out[j][1].iters == last[i][1].iters
+               for j, i in enumerate(pick))
+    solo_rps = len(pick) / solo_s
+
+    def pct(xs, p):
+        return float(np.percentile(np.asarray(xs), p)) if xs else None
+
+    line = {"metric": "requests/s (LPA or Louvain to convergence per request, continuous batching)",
+            "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "serve2048", "description": WORKLOADS["serve2048"], "requests": R,
+                       "slots": args.serve_slots, "small_n": 8192, "batch_arcs": 1 << 22,
+                       "parallelism": f"replicas x{world}",
+                       "timing": "host wall clock from the first submit to the last result of a burst"},
+            "latency_ms": {"burst_p50": pct(lat, 50), "burst_p99": pct(lat, 99),
+                           "burst_queue_p50": pct(queue, 50),
+                           "open_loop": {"rate_per_s": rate, "p50": pct([r.latency_ms for r in ol], 50),
+                                         "p99": pct([r.latency_ms for r in ol], 99),
+                                         "queue_p50": pct([r.queue_ms for r in ol], 50)}},
+            "mean_batched_with": float(np.mean(packed)), "server_stats": stats,
+            "solo": {"requests_per_s": solo_rps, "sample": int(len(pick)), "same_labels": bool(same),
+                     "how": "the same server API with one worker and packing off"},
+            "speedup_vs_solo": value / solo_rps / world,
+            "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "the value itself is end to end: host buffers in, host labels out"},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(line, f, indent=1)
 
 
 # ------------------------------------------------------------------ batched workload
@@ -393,6 +582,9 @@ def main():
         return
     if args.workload == "batch4096":
         run_batch(args, rank, world, local)
+        return
+    if args.workload == "serve2048":
+        run_serve(args, rank, world, local)
         return
     import numpy as np
     import torch

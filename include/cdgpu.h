@@ -173,6 +173,61 @@ int cd_batch_lpa_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int o
 int cd_batch_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_device,
                          int32_t* levels_out, double* q_out);
 
+/* Serving engine: one GPU answering a stream of requests, each LPA
+ * (Algorithm 1) or Louvain (Algorithm 3) on one graph. The paper runs one
+ * graph per call; this adds continuous batching around the same solvers.
+ * Requests are admitted in arrival order onto `slots` worker threads, each
+ * with its own CUDA stream, as soon as a slot is free and the estimated
+ * device memory of the request fits in what is left of the budget (a
+ * request that does not fit reserves its share, so it is not starved).
+ * Waiting requests with n <= small_n of the same algorithm are packed
+ * block-diagonally, up to batch_arcs arcs, into one cd_batch_* call. Every
+ * request gets the labels a solo run on its graph gives. */
+typedef struct cd_server cd_server; /* opaque */
+
+enum { CD_REQ_LPA = 1, CD_REQ_LOUVAIN = 2 };
+
+typedef struct cd_request_result {
+  int32_t status;       /* CD_OK or the error of the solve */
+  int32_t iters;        /* LPA rounds or Louvain levels */
+  int64_t n;            /* vertices (length of the labels) */
+  double q;             /* Louvain: modularity (Sec. II-C); LPA: 0 */
+  double queue_ms;      /* submit -> start of the solve */
+  double latency_ms;    /* submit -> result ready */
+  int32_t batched_with; /* requests solved in the same call (1 = alone) */
+  int32_t reserved;
+} cd_request_result;
+
+/* Start a server on the current device with parameters p (copied; timing is
+ * ignored), 1 <= slots <= 64 workers, a device-memory budget in bytes (<= 0:
+ * 80% of the free memory now), the packing limits small_n and batch_arcs
+ * (0 turns packing off). Errors: CD_EINVAL, CD_ECUDA. */
+int cd_server_create(const cd_params* p, int32_t slots, int64_t mem_budget_bytes, int64_t small_n,
+                     int64_t batch_arcs, cd_server** out);
+
+/* Queue a request; the graph (HOST arrays in the cd_csr_upload convention,
+ * copied before return) is validated when it runs. *id_out receives its id.
+ * Errors: CD_EINVAL (bad kind or pointers, server stopping), CD_ENOMEM
+ * (larger than the whole budget). */
+int cd_server_submit(cd_server* s, int32_t kind, const void* offsets, int offsets_is_i64,
+                     const int32_t* cols, const int32_t* w, int64_t n, int64_t nnz, int64_t* id_out);
+
+/* Wait up to timeout_ms (< 0: without limit) for request id; on completion
+ * fill *res (may be NULL) and labels_out (host, n int32, may be NULL; written
+ * only on success), forget the request and return its status. CD_ETIMEOUT
+ * if it is not done in time (it stays queued), CD_EINVAL for an unknown id. */
+int cd_server_wait(cd_server* s, int64_t id, int64_t timeout_ms, cd_request_result* res,
+                   int32_t* labels_out);
+
+/* Counters: requests admitted and completed, packed calls made, bytes of the
+ * budget in use. Outputs may be NULL. */
+int cd_server_stats(cd_server* s, int64_t* admitted, int64_t* completed, int64_t* packed_calls,
+                    int64_t* in_use);
+
+/* Finish every queued request, stop the workers and free the server. No
+ * other call on s may run concurrently or follow. */
+int cd_server_destroy(cd_server* s);
+
 /* Degree bins (performance only; results never depend on them): vertices of
  * degree 33..t_warp are scanned by one warp, t_warp+1..t_hub by 128 threads
  * with a shared-memory table, and vertices above t_hub keep persistent label

@@ -28,8 +28,11 @@ EXPORTED = [
     "cd_lpa_run", "cd_louvain_local_move", "cd_louvain_aggregate", "cd_modularity",
     "cd_louvain_run", "cd_trace_get", "cd_profile_get", "cd_status_string", "cd_last_cuda_error",
     "cd_launch_count", "cd_modularity_noalloc", "cd_graph_set_batches", "cd_batch_lpa_run",
-    "cd_batch_louvain_run", "cd_graph_set_bins", "cd_autotune",
+    "cd_batch_louvain_run", "cd_graph_set_bins", "cd_autotune", "cd_server_create", "cd_server_submit",
+    "cd_server_wait", "cd_server_stats", "cd_server_destroy",
 ]
+
+CD_REQ_LPA, CD_REQ_LOUVAIN = 1, 2
 
 
 class cd_params(ctypes.Structure):
@@ -48,6 +51,12 @@ class cd_round_trace(ctypes.Structure):
 class cd_kernel_profile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64),
                 ("total_ms", ctypes.c_double), ("alg_bytes", ctypes.c_double)]
+
+
+class cd_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("q", ctypes.c_double), ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("batched_with", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class CDError(RuntimeError):
@@ -92,6 +101,13 @@ def lib():
         L.cd_autotune.argtypes = [_P, ctypes.POINTER(cd_params), ctypes.c_int32, _P, _P]
         L.cd_batch_lpa_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P]
         L.cd_batch_louvain_run.argtypes = [_P, ctypes.POINTER(cd_params), _P, ctypes.c_int, _P, _P]
+        L.cd_server_create.argtypes = [ctypes.POINTER(cd_params), ctypes.c_int32, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(_P)]
+        L.cd_server_submit.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int, _P, _P, ctypes.c_int64,
+                                       ctypes.c_int64, _P]
+        L.cd_server_wait.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(cd_request_result), _P]
+        L.cd_server_stats.argtypes = [_P, _P, _P, _P, _P]
+        L.cd_server_destroy.argtypes = [_P]
         _lib = L
     return _lib
 
@@ -281,6 +297,43 @@ def cd_status_string(status: int) -> str:
     return lib().cd_status_string(status).decode()
 
 
+def cd_server_create(params: cd_params, slots: int = 4, mem_budget_bytes: int = 0, small_n: int = 4096,
+                     batch_arcs: int = 1 << 24) -> ctypes.c_void_p:
+    h = _P()
+    _check(lib().cd_server_create(ctypes.byref(params), slots, mem_budget_bytes, small_n, batch_arcs,
+                                  ctypes.byref(h)), "cd_server_create")
+    return h
+
+
+def cd_server_submit(s, kind: int, offsets, cols, w=None) -> int:
+    """Queue one request; offsets/cols/w are HOST numpy arrays (copied)."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    w = None if w is None else np.ascontiguousarray(w, dtype=np.int32)
+    rid = ctypes.c_int64()
+    _check(lib().cd_server_submit(s, kind, _ptr(offsets)[0], 1, _ptr(cols)[0], _ptr(w)[0], len(offsets) - 1,
+                                  len(cols), ctypes.byref(rid)), "cd_server_submit")
+    return rid.value
+
+
+def cd_server_wait(s, rid: int, n: int, timeout_ms: int = -1):
+    """(labels (numpy int32), cd_request_result) of a finished request."""
+    res = cd_request_result()
+    labels = np.empty(n, dtype=np.int32)
+    _check(lib().cd_server_wait(s, rid, timeout_ms, ctypes.byref(res), _ptr(labels)[0]), "cd_server_wait")
+    return labels, res
+
+
+def cd_server_stats(s):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().cd_server_stats(s, *[ctypes.byref(x) for x in v]), "cd_server_stats")
+    return {"admitted": v[0].value, "completed": v[1].value, "packed_calls": v[2].value, "in_use": v[3].value}
+
+
+def cd_server_destroy(s) -> None:
+    _check(lib().cd_server_destroy(s), "cd_server_destroy")
+
+
 # ------------------------------------------------------------------ convenience handle
 
 class Graph:
@@ -365,3 +418,41 @@ class Graph:
 
     def profile(self):
         return cd_profile_get(self.h)
+
+
+class Server:
+    """Owns a cd_server; submit() returns an id, result() waits for it."""
+
+    def __init__(self, params=None, slots=4, mem_budget_bytes=0, small_n=4096, batch_arcs=1 << 24, **kw):
+        params = params or cd_params_default(**kw)
+        self.h = cd_server_create(params, slots, mem_budget_bytes, small_n, batch_arcs)
+        self._n = {}
+
+    def submit(self, kind, offsets, cols, w=None) -> int:
+        rid = cd_server_submit(self.h, kind, offsets, cols, w)
+        self._n[rid] = len(offsets) - 1
+        return rid
+
+    def result(self, rid, timeout_ms=-1):
+        try:
+            labels, res = cd_server_wait(self.h, rid, self._n[rid], timeout_ms)
+        except CDError as e:
+            if e.status != CD_ETIMEOUT:  # the request is finished (failed)
+                self._n.pop(rid, None)
+            raise
+        del self._n[rid]
+        return labels, res
+
+    def stats(self):
+        return cd_server_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

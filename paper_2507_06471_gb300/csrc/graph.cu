@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cd {
@@ -34,8 +36,9 @@ int set_cuda_error(cudaError_t e) {
 }
 
 int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
-  static bool pool_set = false;
-  if (!pool_set) {
+  // keep freed blocks in the device's default pool (threads may race here)
+  static std::once_flag pool_set;
+  std::call_once(pool_set, [] {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaMemPool_t pool;
@@ -43,8 +46,7 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t s) {
       uint64_t thr = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
-    pool_set = true;
-  }
+  });
   cudaError_t e = cudaMallocAsync(p, bytes, s);
   if (e != cudaSuccess) {
     *p = nullptr;

@@ -14,11 +14,15 @@
 // A vertex whose decision differs from its label commits only if the pinned
 // SplitMix64 coin says so; otherwise it defers and stays active.
 //
-// Degree bins (static per graph): degrees 1-4/5-8/9-16/17-32 use TILE lanes
-// per vertex and group equal labels with __match_any_sync; 33-256 a warp with
-// a shared-memory open-addressing table; 257-4096 a CTA with a shared-memory
-// table; larger degrees (hubs) insert into per-hub global tables from many
-// CTAs, then many CTAs evaluate slices of the table and the last one decides.
+// Degree bins (per graph, thresholds t_warp <= t_hub, defaults 256 and
+// 1024): degrees 1-4/5-8/9-16/17-32 use TILE lanes per vertex and group equal
+// labels with __match_any_sync; 33..t_warp a warp with a shared-memory
+// open-addressing table; up to t_hub 128 threads with a shared-memory table;
+// larger degrees (hubs) keep persistent label histograms in global memory,
+// updated by their neighbours' moves, and many CTAs evaluate slices of a
+// hub's histogram with the last one deciding.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace cd {
@@ -818,7 +822,7 @@ template <class V> constexpr size_t hub_smem() { return group_smem<V>(1, HUB_CAP
 
 template <bool LOUV, class W, class V>
 int set_smem_attrs() {
-  static bool done = false;
+  static std::atomic<bool> done{false};  // idempotent; threads may race here
   if (done) return CD_OK;
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
