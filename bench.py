@@ -46,6 +46,10 @@ WORKLOADS = {
     "serve2048": "stream of 2,048 requests (1/3 LPA, 2/3 Louvain, seeded): 1,984 planted-partition SBM "
                  "graphs as in batch4096, 48 SBM graphs with n log-uniform in [10,000, 30,000] and "
                  "blocks of 100, 16 R-MAT graphs of scale 14-17 (edge factor 16); host buffers",
+    "served": "the first --serve-requests of a 20,000-request stream, seed 5: n log-uniform in [100, 2e6], "
+              "70% Louvain / 30% LPA, half R-MAT (edge factor 8 at scale ceil(log2 n), endpoints >= n "
+              "rejected), half edge-sampled planted partition (k uniform in {2..50}, mean degree 16, "
+              "p_out = p_in / 100); unit weights; host buffers",
 }
 
 
@@ -62,6 +66,8 @@ def parse():
     ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-requests", type=int, default=512,
+                    help="served: how many requests of the 20,000-request stream to run")
     ap.add_argument("--solo-sample", type=int, default=128,
                     help="batch workload: graphs timed one call per graph for the comparison")
     return ap.parse_args()
@@ -257,7 +263,7 @@ def run_reference(args, rank, world):
     """The oracle on the host cores, timed on bounded samples of the workload."""
     if rank != 0:
         return
-    if args.workload in ("batch4096", "serve2048"):
+    if args.workload in ("batch4096", "serve2048", "served"):
         run_reference_many(args)
         return
     import torch
@@ -294,7 +300,8 @@ def run_reference_many(args, budget_s: float = 20.0):
         reqs = [(2, *host_graph(synth.sbm(n, k, "0.2", "0.002", seed=sd, wmax=4)))
                 for n, k, sd in synth.batch_specs(4096, seed=4)[:64]]
     else:
-        reqs = [(k, o, c, None if w is None else w.astype(np.int64)) for k, o, c, w in serve_requests(11)]
+        reqs = [(k, o, c, None if w is None else w.astype(np.int64))
+                for k, o, c, w in serve_requests(args.workload, 11, min(args.serve_requests, 64))]
     per_step = max(1.0, budget_s / max(1, args.steps + args.warmup))
     done, secs, i = 0, 0.0, 0
     for step in range(args.warmup + args.steps):
@@ -325,13 +332,47 @@ def run_reference_many(args, budget_s: float = 20.0):
 
 # ------------------------------------------------------------------ serving workload
 
-def serve_requests(seed: int):
-    """The serve2048 request stream as host arrays: [(kind, off int64, cols int32, w int32|None)]."""
+def host_mem_available() -> int:
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def _host_req(kind, g):
+    import numpy as np
+    off = g.off.cpu().numpy().astype(np.int64)
+    cols = g.cols.cpu().numpy().astype(np.int32)
+    w = None if g.w is None else g.w.cpu().numpy().astype(np.int32)
+    return (kind, off, cols, w)
+
+
+def serve_requests(workload: str, seed: int, count: int = 0):
+    """A request stream as host arrays: [(kind, off int64, cols int32, w int32|None)], kind 1 = LPA,
+    2 = Louvain. serve2048: mostly small graphs (packing); served: the heavy-tailed size mix."""
     import numpy as np
     import torch
 
     import synth
     dev = "cuda" if torch.cuda.is_available() else "cpu"
+    if workload == "served":
+        specs = synth.serve_specs(20_000, seed=5)[:count or 512]
+        # host memory guard: the stream is held twice (here and in the server's queue)
+        avail = host_mem_available()
+        need = 0
+        for i, sp in enumerate(specs):
+            need += 2 * (sp[2] * 16 * 4 + sp[2] * 8)
+            if avail and need > avail // 4:
+                specs = specs[:i]
+                break
+        out = []
+        for sp in specs:
+            out.append(_host_req(2 if sp[0] == "louvain" else 1, synth.serve_graph(sp, dev)))
+        return out
     rng = np.random.default_rng(seed)
     small = synth.batch_specs(1984, seed=seed)
     mid_n = np.exp(rng.uniform(np.log(10_000), np.log(30_000), 48)).astype(np.int64)
@@ -347,19 +388,14 @@ def serve_requests(seed: int):
         graphs.append(synth.rmat(14 + j % 4, 16, seed=seed * 100 + j, device=dev).to("cpu"))
     order = rng.permutation(len(graphs))
     kinds = rng.integers(0, 3, len(graphs))
-    out = []
-    for i, o in enumerate(order):
-        g = graphs[o]
-        off = g.off.numpy().astype(np.int64)
-        cols = g.cols.numpy().astype(np.int32)
-        w = None if g.w is None else g.w.numpy().astype(np.int32)
-        out.append((1 if kinds[i] == 0 else 2, off, cols, w))
-    return out
+    return [_host_req(1 if kinds[i] == 0 else 2, graphs[o]) for i, o in enumerate(order)]
 
 
 def run_serve(args, rank, world, local):
     """Requests through the serving engine (continuous batching over worker
-    streams) vs the same requests one call at a time."""
+    streams) vs the same requests one call at a time: throughput when all
+    arrive at once, and latency under Poisson arrivals at 0.8x the measured
+    one-at-a-time capacity, for both."""
     import threading
 
     import numpy as np
@@ -368,35 +404,62 @@ def run_serve(args, rank, world, local):
     import paper_2507_06471_gb300 as cd
 
     cd.lib()
-    reqs = serve_requests(11 + 7919 * rank)
+    reqs = serve_requests(args.workload, 11 + 7919 * rank, args.serve_requests)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     R = len(reqs)
     h2d = sum(o.nbytes + c.nbytes + (0 if w is None else w.nbytes) for _, o, c, w in reqs)
     d2h = sum(4 * (len(o) - 1) for _, o, _, _ in reqs)
+    arcs = sum(len(c) for _, _, c, _ in reqs)
 
-    def burst(srv, subset=None):
-        rs = reqs if subset is None else [reqs[i] for i in subset]
+    def burst(srv):
         t0 = time.perf_counter()
-        ids = [srv.submit(k, o, c, w) for k, o, c, w in rs]
+        ids = [srv.submit(k, o, c, w) for k, o, c, w in reqs]
         out = [srv.result(i) for i in ids]
         return time.perf_counter() - t0, out
 
-    srv = cd.Server(slots=args.serve_slots, small_n=8192, batch_arcs=1 << 22)
-    for _ in range(args.warmup):
+    def open_loop(srv, rate, seed=5):
+        gaps = np.random.default_rng(seed).exponential(1.0 / rate, R)
+        ids = []
+
+        def feed():
+            t = time.perf_counter()
+            for i, (k, o, c, w) in enumerate(reqs):
+                t += gaps[i]
+                d = t - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                ids.append(srv.submit(k, o, c, w))
+
+        th = threading.Thread(target=feed)
+        th.start()
+        th.join()
+        res = [srv.result(i)[1] for i in ids]
+        lat = [r.latency_ms for r in res]
+        return {"rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(np.max(lat)),
+                "queue_p50_ms": float(np.percentile([r.queue_ms for r in res], 50))}
+
+    small_n, batch_arcs = 8192, 1 << 22
+    srv = cd.Server(slots=args.serve_slots, small_n=small_n, batch_arcs=batch_arcs)
+    seq = cd.Server(slots=1, small_n=0)
+    for _ in range(max(1, args.warmup)):
         burst(srv)
+    # one call at a time: capacity and labels
+    seq_s, seq_out = burst(seq)
+    seq_rps = R / seq_s
+
     clocks = ClockSampler(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     launches0 = cd.cd_launch_count()
-    secs, lat, queue, packed = [], [], [], []
+    secs, lat, packed = [], [], []
     last = None
     for _ in range(args.steps):
         dt, last = burst(srv)
         secs.append(dt)
         lat += [r.latency_ms for _, r in last]
-        queue += [r.queue_ms for _, r in last]
         packed += [r.batched_with for _, r in last]
     torch.cuda.synchronize()
     barrier(world)
@@ -405,57 +468,30 @@ def run_serve(args, rank, world, local):
     wall = allreduce_max(sum(secs), world)
     value = allreduce_sum(float(R * args.steps), world) / wall
     stats = srv.stats()
+    same = all(np.array_equal(a[0], b[0]) and a[1].iters == b[1].iters for a, b in zip(seq_out, last))
 
-    # open loop: Poisson arrivals at half the measured throughput of this rank
-    rate = 0.5 * R * args.steps / sum(secs)
-    gaps = np.random.default_rng(5).exponential(1.0 / rate, R)
-    ids = []
-
-    def feed():
-        t = time.perf_counter()
-        for i, (k, o, c, w) in enumerate(reqs):
-            t += gaps[i]
-            d = t - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            ids.append(srv.submit(k, o, c, w))
-
-    th = threading.Thread(target=feed)
-    th.start()
-    th.join()
-    ol = [srv.result(i)[1] for i in ids]
+    rate = 0.8 * seq_rps
+    ol_srv = open_loop(srv, rate)
+    ol_seq = open_loop(seq, rate)
     srv.close()
-
-    # one call at a time (no packing, one worker) on an evenly spaced sample
-    pick = np.linspace(0, R - 1, min(256, R)).astype(int)
-    solo = cd.Server(slots=1, small_n=0)
-    burst(solo, pick[:8])
-    solo_s, solo_out = burst(solo, pick)
-    solo.close()
-    same = all(np.array_equal(solo_out[j][0], last[i][0]) and solo_out[j][1].iters == last[i][1].iters
-               for j, i in enumerate(pick))
-    solo_rps = len(pick) / solo_s
-
-    def pct(xs, p):
-        return float(np.percentile(np.asarray(xs), p)) if xs else None
+    seq.close()
 
     line = {"metric": "requests/s (LPA or Louvain to convergence per request, continuous batching)",
             "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": "serve2048", "description": WORKLOADS["serve2048"], "requests": R,
-                       "slots": args.serve_slots, "small_n": 8192, "batch_arcs": 1 << 22,
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "requests": R,
+                       "arcs": arcs, "slots": args.serve_slots, "small_n": small_n, "batch_arcs": batch_arcs,
                        "parallelism": f"replicas x{world}",
-                       "timing": "host wall clock from the first submit to the last result of a burst"},
-            "latency_ms": {"burst_p50": pct(lat, 50), "burst_p99": pct(lat, 99),
-                           "burst_queue_p50": pct(queue, 50),
-                           "open_loop": {"rate_per_s": rate, "p50": pct([r.latency_ms for r in ol], 50),
-                                         "p99": pct([r.latency_ms for r in ol], 99),
-                                         "queue_p50": pct([r.queue_ms for r in ol], 50)}},
+                       "timing": "host wall clock from the first submit to the last result; all requests "
+                                 "submitted at once"},
+            "latency_ms_all_at_once": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "open_loop": {"arrivals": "Poisson at 0.8x the measured one-at-a-time capacity",
+                          "server": ol_srv, "one_at_a_time": ol_seq},
             "mean_batched_with": float(np.mean(packed)), "server_stats": stats,
-            "solo": {"requests_per_s": solo_rps, "sample": int(len(pick)), "same_labels": bool(same),
-                     "how": "the same server API with one worker and packing off"},
-            "speedup_vs_solo": value / solo_rps / world,
+            "one_at_a_time": {"requests_per_s": seq_rps, "same_labels_and_iters": bool(same),
+                              "how": "the same server API with one worker and packing off"},
+            "speedup_vs_one_at_a_time": value / seq_rps / world,
             "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": "the value itself is end to end: host buffers in, host labels out"},
             "gpu_launches": launches, "clocks": clk}
@@ -583,7 +619,7 @@ def main():
     if args.workload == "batch4096":
         run_batch(args, rank, world, local)
         return
-    if args.workload == "serve2048":
+    if args.workload in ("serve2048", "served"):
         run_serve(args, rank, world, local)
         return
     import numpy as np

@@ -266,6 +266,9 @@ def _gpu_lib():
         L.synth_sbm_rows.restype = ctypes.c_int
         L.synth_sbm_rows.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        L.synth_sbm_edges.restype = ctypes.c_int
+        L.synth_sbm_edges.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_void_p, ctypes.c_void_p]
         L.synth_rmat_keys.restype = ctypes.c_int
         L.synth_rmat_keys.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                       ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
@@ -320,6 +323,108 @@ def rmat(scale: int, edge_factor: int = 16, a="0.57", b="0.19", c="0.19", seed: 
     g = csr_from_edge_keys(keys, n, None)
     g.name = f"rmat{scale}_ef{edge_factor}" + ("_perm" if permute else "")
     return g
+
+
+# ------------------------------------------------- served request stream
+
+TAG_SERVE = 0x53455256
+TAG_SBMS = 0x53424D53
+
+
+def _pick32(r: np.ndarray, span) -> np.ndarray:
+    """Uniform integer in [0, span) from the top 32 bits (multiply-shift)."""
+    return ((r >> np.uint64(32)) * np.asarray(span, dtype=np.uint64)) >> np.uint64(32)
+
+
+def sbm_sparse_keys_host(n: int, k: int, m: int, seed: int) -> np.ndarray:
+    """Edge-sampled planted partition: m candidate edges, edge j from draws
+    3j, 3j+1, 3j+2: u uniform; it stays in u's block (size s) with
+    probability 100 (s-1) / (100 (s-1) + n - s), i.e. p_out = p_in / 100,
+    then v is uniform in the block, else uniform over the other n - s
+    vertices. Keys lo*2^32+hi, loops -> -1. Same definition as the device
+    kernel in rmat_gpu.cu."""
+    if not 1 <= n <= 40_000_000:
+        raise ValueError("n out of range")
+    key = stream_key(seed, TAG_SBMS)
+    bsz = max(n // k, 1)
+    j = np.arange(m, dtype=np.uint64) * np.uint64(3)
+    u = _pick32(draw(key, j), n).astype(np.int64)
+    bu = np.minimum(u // bsz, k - 1)
+    b0 = bu * bsz
+    s = np.where(bu == k - 1, n - b0, bsz)
+    in_w = (100 * (s - 1)).astype(np.uint64)
+    out_w = (n - s).astype(np.uint64)
+    tot = in_w + out_w
+    same = _pick32(draw(key, j + np.uint64(1)), tot) < in_w
+    r2 = draw(key, j + np.uint64(2))
+    v_in = b0 + _pick32(r2, s.astype(np.uint64)).astype(np.int64)
+    x = _pick32(r2, out_w).astype(np.int64)
+    v_out = np.where(x < b0, x, x + s)
+    v = np.where(tot == 0, u, np.where(same, v_in, v_out))
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    return np.where(lo == hi, -1, lo * (1 << 32) + hi)
+
+
+def sbm_sparse(n: int, k: int, mean_deg: int = 16, seed: int = 5, device: str = "cpu") -> Graph:
+    """Sparse planted-partition graph of about mean_deg * n / 2 edges (see
+    sbm_sparse_keys_host), deduplicated, loops removed, unit weights, ids
+    unpermuted (blocks are contiguous id ranges)."""
+    m = n * mean_deg // 2
+    if device == "cpu":
+        keys = torch.from_numpy(sbm_sparse_keys_host(n, k, m, seed))
+    else:
+        keys = torch.empty(m, dtype=torch.int64, device=device)
+        stream = torch.cuda.current_stream(keys.device).cuda_stream
+        rc = _gpu_lib().synth_sbm_edges(stream_key(seed, TAG_SBMS), n, k, m, ctypes.c_void_p(keys.data_ptr()),
+                                        ctypes.c_void_p(stream))
+        if rc != 0:
+            raise RuntimeError(f"synth_sbm_edges failed: {rc}")
+    keys = torch.unique(keys[keys >= 0], sorted=True)
+    g = csr_from_edge_keys(keys, n, None)
+    g.planted = np.minimum(np.arange(n) // max(n // k, 1), k - 1).astype(np.int32)
+    g.name = f"sbms_n{n}_k{k}"
+    return g
+
+
+def rmat_n(n: int, edge_factor: int = 8, seed: int = 5, device: str = "cpu", a="0.57", b="0.19",
+           c="0.19") -> Graph:
+    """R-MAT on n vertices: edge_factor * 2^scale edges drawn at scale =
+    ceil(log2 n), edges with an endpoint >= n rejected, then deduplicated,
+    symmetrised, loops removed, unit weights."""
+    scale = max(1, int(n - 1).bit_length())
+    if device == "cpu":
+        keys = torch.from_numpy(rmat_keys_host(scale, edge_factor, a, b, c, seed))
+    else:
+        keys = rmat_keys_device(scale, edge_factor, a, b, c, seed, device)
+    keys = keys[(keys >= 0) & ((keys & 0xFFFFFFFF) < n)]
+    keys = torch.unique(keys, sorted=True)
+    g = csr_from_edge_keys(keys, n, None)
+    g.name = f"rmatn{n}_ef{edge_factor}"
+    return g
+
+
+def serve_specs(count: int, seed: int = 5, nmin: int = 100, nmax: int = 2_000_000):
+    """Seeded served-request recipe: per request (kind, family, n, k, graph
+    seed) with n log-uniform in [nmin, nmax], kind "louvain" with probability
+    0.7 else "lpa", family "rmat" or "sbm" with probability 1/2 each, k
+    uniform in {2..50} (SBM blocks)."""
+    key = stream_key(seed, TAG_SERVE)
+    r = draw(key, np.arange(4 * count, dtype=np.uint64)).reshape(count, 4)
+    u = (r[:, 0] >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    ns = np.clip(np.floor(np.exp(np.log(nmin) + u * (np.log(nmax + 1) - np.log(nmin)))), nmin, nmax).astype(np.int64)
+    louv = (r[:, 1] >> np.uint64(32)) < np.uint64(threshold32("0.7"))
+    rm = (r[:, 2] >> np.uint64(63)) == np.uint64(1)
+    ks = uniform_int(r[:, 3], 2, 50)
+    return [("louvain" if louv[i] else "lpa", "rmat" if rm[i] else "sbm", int(ns[i]), int(min(ks[i], ns[i])),
+             (seed << 24) + i) for i in range(count)]
+
+
+def serve_graph(spec, device: str = "cpu") -> Graph:
+    """The graph of one served request (see serve_specs)."""
+    _, family, n, k, sd = spec
+    if family == "rmat":
+        return rmat_n(n, 8, seed=sd, device=device)
+    return sbm_sparse(n, k, 16, seed=sd, device=device)
 
 
 # -------------------------------------------------------------- LFR-style

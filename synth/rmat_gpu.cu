@@ -66,7 +66,51 @@ __global__ void sbm_rows_kernel(const int64_t* __restrict__ vstart, const int32_
   }
 }
 
+// Edge-sampled planted partition (for sparse graphs too large for the
+// pairwise definition): edge j takes draws 3j, 3j+1, 3j+2 of the stream. Its
+// first endpoint u is uniform on [0, n); with block size s of u's block it
+// stays inside that block with probability 100 (s-1) / (100 (s-1) + n - s)
+// (p_out = p_in / 100) and then v is uniform in the block, else v is uniform
+// over the other n - s vertices. Uniform picks are multiply-shift on the top
+// 32 bits (spans stay below 2^32 for n <= 4e7). Loops give -1; keys are
+// lo << 32 | hi.
+__device__ __forceinline__ uint64_t pick32(uint64_t r, uint64_t span) { return ((r >> 32) * span) >> 32; }
+
+__global__ void sbm_edges_kernel(uint64_t key, int64_t n, int64_t k, int64_t m, int64_t* __restrict__ out) {
+  int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t bsz = n / k;
+  if (bsz < 1) bsz = 1;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += stride) {
+    const uint64_t c = 3ull * (uint64_t)j;
+    const int64_t u = (int64_t)pick32(sm64_draw(key, c), (uint64_t)n);
+    const int64_t bu = u / bsz < k - 1 ? u / bsz : k - 1;
+    const int64_t b0 = bu * bsz;
+    const int64_t s = bu == k - 1 ? n - b0 : bsz;
+    const uint64_t in_w = 100ull * (uint64_t)(s - 1), out_w = (uint64_t)(n - s);
+    int64_t v = u;
+    if (in_w + out_w > 0) {
+      if (pick32(sm64_draw(key, c + 1), in_w + out_w) < in_w) {
+        v = b0 + (int64_t)pick32(sm64_draw(key, c + 2), (uint64_t)s);
+      } else {
+        const int64_t x = (int64_t)pick32(sm64_draw(key, c + 2), out_w);
+        v = x < b0 ? x : x + s;
+      }
+    }
+    const int64_t lo = u < v ? u : v, hi = u < v ? v : u;
+    out[j] = lo == hi ? -1 : (lo << 32) | hi;
+  }
+}
+
 }  // namespace
+
+extern "C" int synth_sbm_edges(uint64_t key, int64_t n, int64_t k, int64_t m, void* out, void* stream) {
+  if (n < 1 || n > 40000000 || k < 1 || m < 0 || (m > 0 && out == nullptr)) return -1;
+  if (m == 0) return 0;
+  int64_t blocks = (m + 255) / 256;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  sbm_edges_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(key, n, k, m, (int64_t*)out);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
 
 extern "C" int synth_sbm_rows(const void* vstart, const void* row_graph, const void* blocks, const void* keys,
                               uint64_t t_in, uint64_t t_out, int64_t rows, void* out, void* out_n, int64_t cap,

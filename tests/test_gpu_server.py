@@ -204,3 +204,33 @@ def test_destroy_drains_queue():
         srv.submit(cd.CD_REQ_LOUVAIN, *_host(g))
     cd.cd_server_destroy(srv.h)  # returns after every queued request ran
     srv.h = None
+
+
+def test_served_generators_device_equals_host():
+    for n, k, sd in [(5000, 7, 1), (777, 2, 2), (100, 50, 3)]:
+        h = synth.sbm_sparse(n, k, 16, seed=sd)
+        d = synth.sbm_sparse(n, k, 16, seed=sd, device="cuda").to("cpu")
+        assert torch_equal(h, d)
+    for n, sd in [(3000, 4), (4096, 5), (100, 6)]:
+        assert torch_equal(synth.rmat_n(n, 8, seed=sd), synth.rmat_n(n, 8, seed=sd, device="cuda").to("cpu"))
+
+
+def torch_equal(a, b):
+    import torch
+    return a.n == b.n and torch.equal(a.off, b.off) and torch.equal(a.cols, b.cols) and (a.w is None) == (b.w is None)
+
+
+def test_served_mix_matches_oracle():
+    # the served recipe with sizes capped so the oracle stays quick
+    import paper_2507_06471_gb300 as cd
+    specs = synth.serve_specs(40, seed=9, nmax=30_000)
+    srv = cd.Server(slots=4, small_n=8192, batch_arcs=1 << 20)
+    items = []
+    for sp in specs:
+        g = synth.serve_graph(sp, "cuda").to("cpu")
+        kind = cd.CD_REQ_LOUVAIN if sp[0] == "louvain" else cd.CD_REQ_LPA
+        items.append((srv.submit(kind, *_host(g)), kind, g))
+    for rid, kind, g in items:
+        labels, res = srv.result(rid)
+        _check(res, labels, _expect(kind, g))
+    srv.close()
