@@ -60,7 +60,7 @@ enum Ctr {
 enum Kern {
   K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLK128,
   K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
-  K_COUNT
+  K_HUB_MARK, K_FRONTIER, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -79,6 +79,11 @@ struct cd_graph {
   // static degree bins
   int32_t* bin_list = nullptr;           // n vertex ids grouped by bin
   int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
+  // frontier: the active vertices of a round, bin b at act_list + bin_start[b]
+  int32_t* act_list = nullptr;
+  unsigned long long* act_cnt = nullptr;   // NBINS+1: active per bin, then active hub evaluate items
+  unsigned long long* full_cnt = nullptr;  // NBINS+1: every listed vertex per bin, then every item
+  int32_t* act_ev = nullptr;               // hub_eval_items: evaluate items of the active hubs
   // hubs (degree > BLOCK_MAX): one persistent label histogram per hub, kept in
   // step with the labels by the moves of its neighbours: an open-addressing
   // table of cap_h = 1.5 deg + 64 slots in [hub_tab[h], hub_tab[h+1]). A slot
@@ -100,7 +105,14 @@ struct cd_graph {
   int32_t* hub_hascur = nullptr;           // nhubs
   int32_t* hub_done = nullptr;             // nhubs: finished evaluate items this round
   int32_t* hub_mv = nullptr;               // 3 x nhubs: moved flag, old label, new label
-  int32_t* hub_build = nullptr;            // 1: tables must be rebuilt before the next scan
+  int32_t* hub_rb = nullptr;               // nhubs: 1 = rebuild this hub's table from its row
+  int32_t* hub_flist = nullptr;            // 2 x nhubs: hubs flagged in even / odd rounds
+  unsigned long long* hub_fcnt = nullptr;  // 2: their counts
+  int32_t* hub_used = nullptr;             // nhubs: slots claimed since the last build
+  int64_t* hub_item_first = nullptr;       // nhubs+1: first build/mark item of each hub
+  int32_t* hub_blist = nullptr;            // hub_items: build items queued this round
+  int32_t* hub_mlist = nullptr;            // hub_items: mark items queued this round
+  unsigned long long* hub_lcnt = nullptr;  // 2: queued build and mark items
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
   int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads; above: hub

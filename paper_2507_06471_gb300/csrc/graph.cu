@@ -19,7 +19,7 @@ namespace cd {
 const char* const kKernelNames[K_COUNT] = {
     "ingest",     "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
     "scan_blk128", "hub_build", "hub_eval",   "apply_moves", "renumber",    "agg_emit",
-    "radix_sort", "agg_reduce", "modularity"};
+    "radix_sort", "agg_reduce", "modularity", "hub_mark", "frontier"};
 
 static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};
@@ -305,10 +305,13 @@ int read_status(cd_graph* g) {
 void free_arrays(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
+                g->act_list,     g->act_cnt,       g->full_cnt,     g->act_ev,
                 g->hub_idx,      g->hub_bits,      g->hub_tab,       g->hub_slot,
                 g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
-                g->hub_mv,       g->hub_build,     g->C,            g->sigma,        g->csize,
+                g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
+                g->hub_flist,    g->hub_fcnt,
+                g->hub_blist,    g->hub_mlist,     g->hub_lcnt,     g->C,            g->sigma,        g->csize,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
                 g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
                 g->gfrozen,      g->gcnt};
@@ -318,12 +321,19 @@ void free_arrays(cd_graph* g) {
 
 void free_bins(cd_graph* g) {
   cudaStream_t s = g->stream;
-  void* ps[] = {g->bin_list,     g->hub_idx,     g->hub_bits,     g->hub_tab,   g->hub_slot,
+  void* ps[] = {g->bin_list,     g->act_list,    g->act_cnt,      g->full_cnt,  g->act_ev,
+                g->hub_idx,      g->hub_bits,     g->hub_tab,   g->hub_slot,
                 g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
-                g->hub_build};
+                g->hub_rb,       g->hub_used,     g->hub_item_first, g->hub_blist,
+                g->hub_flist,    g->hub_fcnt,
+                g->hub_mlist,    g->hub_lcnt};
   for (void* p : ps) dev_free(p, s);
   g->bin_list = nullptr;
+  g->act_list = nullptr;
+  g->act_cnt = nullptr;
+  g->full_cnt = nullptr;
+  g->act_ev = nullptr;
   g->hub_idx = nullptr;
   g->hub_bits = nullptr;
   g->hub_tab = nullptr;
@@ -338,7 +348,14 @@ void free_bins(cd_graph* g) {
   g->hub_hascur = nullptr;
   g->hub_done = nullptr;
   g->hub_mv = nullptr;
-  g->hub_build = nullptr;
+  g->hub_rb = nullptr;
+  g->hub_flist = nullptr;
+  g->hub_fcnt = nullptr;
+  g->hub_used = nullptr;
+  g->hub_item_first = nullptr;
+  g->hub_blist = nullptr;
+  g->hub_mlist = nullptr;
+  g->hub_lcnt = nullptr;
   g->nhubs = g->hub_slots = g->hub_items = g->hub_eval_items = 0;
 }
 
@@ -374,6 +391,9 @@ int build_bins(cd_graph* g) {
   int64_t listed = g->bin_start[NBINS];
   rc = dev_alloc_t(&g->bin_list, listed, s);
   if (rc) return rc;
+  if ((rc = dev_alloc_t(&g->act_list, listed, s))) return rc;
+  if ((rc = dev_alloc_t(&g->act_cnt, NBINS + 1, s))) return rc;
+  if ((rc = dev_alloc_t(&g->full_cnt, NBINS + 1, s))) return rc;
   int64_t* d_base = nullptr;
   unsigned long long* d_cur = nullptr;
   if ((rc = dev_alloc_t(&d_base, NBINS, s))) return rc;
@@ -396,12 +416,13 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaMemcpyAsync(rows.data(), d_rows, 2 * nh * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     CD_CHECK(cudaStreamSynchronize(s));
     dev_free(d_rows, s);
-    std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0), ev_slot;
+    std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0), ev_slot, item_first(nh + 1, 0);
     std::vector<int32_t> item_hub, ev_hub;
     for (int64_t h = 0; h < nh; ++h) {
       int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
       int64_t cap = deg + deg / 2 + 64;  // live labels <= deg; the rest absorbs labels that come and go
       tab[h + 1] = tab[h] + cap;
+      item_first[h] = (int64_t)item_hub.size();
       for (int64_t a = 0; a < deg; a += HUB_CHUNK) {
         item_hub.push_back((int32_t)h);
         item_arc.push_back(beg + a);
@@ -413,9 +434,11 @@ int build_bins(cd_graph* g) {
       }
     }
     ev_first[nh] = (int64_t)ev_hub.size();
+    item_first[nh] = (int64_t)item_hub.size();
     g->hub_slots = tab[nh];
     g->hub_items = (int64_t)item_hub.size();
     g->hub_eval_items = (int64_t)ev_hub.size();
+    if ((rc = dev_alloc_t(&g->act_ev, g->hub_eval_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_idx, g->n, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_bits, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
@@ -431,13 +454,25 @@ int build_bins(cd_graph* g) {
     if ((rc = dev_alloc_t(&g->hub_hascur, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_done, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_mv, 3 * nh, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_build, 1, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_rb, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_flist, 2 * nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_fcnt, 2, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_used, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_item_first, nh + 1, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_blist, g->hub_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_mlist, g->hub_items, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_lcnt, 2, s))) return rc;
     CD_CHECK(cudaMemcpyAsync(g->hub_tab, tab.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_hub, item_hub.data(), item_hub.size() * 4, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_arc, item_arc.data(), item_arc.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_hub, ev_hub.data(), ev_hub.size() * 4, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_slot, ev_slot.data(), ev_slot.size() * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_ev_first, ev_first.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemcpyAsync(g->hub_item_first, item_first.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_rb, 0, nh * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_used, 0, nh * 4, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * 8, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_fcnt, 0, 2 * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
@@ -446,6 +481,13 @@ int build_bins(cd_graph* g) {
     CD_LAUNCH(k_hub_index<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
                                                                        g->hub_idx, g->hub_bits));
     CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
+  }
+  {
+    unsigned long long full[NBINS + 1];
+    for (int b = 0; b < NBINS; ++b) full[b] = (unsigned long long)(g->bin_start[b + 1] - g->bin_start[b]);
+    full[NBINS] = (unsigned long long)g->hub_eval_items;
+    CD_CHECK(cudaMemcpyAsync(g->full_cnt, full, sizeof(full), cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaStreamSynchronize(s));  // `full` lives on this stack frame
   }
   dev_free(d_base, s);
   dev_free(d_cur, s);

@@ -21,7 +21,10 @@
 // larger degrees (hubs) keep persistent label histograms in global memory,
 // updated by their neighbours' moves, and many CTAs evaluate slices of a
 // hub's histogram with the last one deciding.
+#include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 
@@ -32,6 +35,8 @@ constexpr int NT = 256;  // threads of the tile and hub-evaluate kernels
 constexpr int NW = NT / 32;
 constexpr int WARP_CAP_SLOTS = 2 * WARP_MAX;   // table slots per warp-bin vertex
 constexpr int BLK1_CAP_SLOTS = 2 * BLK1_MAX;   // per 128-thread group
+constexpr bool BLK_PF = false;  // header prefetch in the 128-thread group kernel
+constexpr int BLK_WAVES = 1;    // grid of the 128-thread group kernel, in resident waves
 
 // ------------------------------------------------------------------ coin
 
@@ -118,7 +123,18 @@ struct ScanCtx {
   int32_t* hub_hascur;
   int32_t* hub_done;
   int32_t* hub_mv;
-  int32_t* hub_build;
+  int32_t* hub_rb;                   // per hub: 1 = rebuild from its row before its next evaluation
+  int32_t* hub_flist_w;              // hubs flagged this round (read back at the start of the next)
+  unsigned long long* hub_fcnt_w;
+  const int32_t* hub_flist_r;        // hubs flagged in the previous round
+  const unsigned long long* hub_fcnt_r;
+  int32_t* hub_used;                 // per hub: slots claimed since its last build
+  const int64_t* hub_item_first;     // nhubs+1: first build/mark item of each hub
+  int32_t* hub_blist;                // build items of the hubs being rebuilt this round
+  int32_t* hub_mlist;                // mark items of the hubs that moved this round
+  unsigned long long* hub_lcnt;      // [0] build items, [1] mark items
+  const int32_t* ev_list;            // evaluate items to run this round (null: all of them)
+  const unsigned long long* ev_cnt;  // their number
   int64_t n_items, nhubs, n_ev_items;
   // batched mode (gid == nullptr: one graph)
   const int32_t* gid;
@@ -147,6 +163,15 @@ __device__ __forceinline__ typename KeyOf<LOUV>::T cand_key(const ScanCtx& s, in
                                                             int64_t d, int64_t vol) {
   if constexpr (LOUV)
     return (i128)vol * k - (i128)d * s.sigma[c];
+  else
+    return k;
+}
+
+// The same key with Sigma_tot[c] already loaded.
+template <bool LOUV>
+__device__ __forceinline__ typename KeyOf<LOUV>::T cand_key_sg(int64_t sig, int64_t k, int64_t d, int64_t vol) {
+  if constexpr (LOUV)
+    return (i128)vol * k - (i128)d * sig;
   else
     return k;
 }
@@ -232,24 +257,45 @@ __device__ __forceinline__ int64_t group_sum(unsigned peers, int64_t wt, int64_t
 
 constexpr unsigned long long SLOT_EMPTY = ~0ull;
 
+// Flag hub h to be rebuilt from its row at the start of the next round; its
+// histogram is not updated until then. A hub is queued once, when first
+// flagged.
+__device__ __forceinline__ void hub_flag_rebuild(const ScanCtx& s, int32_t h) {
+  if (atomicExch(&s.hub_rb[h], 1) == 0) s.hub_flist_w[atomicAdd(s.hub_fcnt_w, 1ull)] = h;
+}
+
+// An update gives up after HUB_PROBE_MAX probes, and a hub whose claimed
+// slots pass 7/8 of its capacity is rebuilt: labels that leave keep their
+// slot (count 0), so a table fills up over the rounds and linear-probe chains
+// would otherwise grow without bound.
+constexpr int HUB_PROBE_MAX = 64;
+
 // k_{h,label} += w in hub h's histogram (w may be negative: a neighbour left
 // `label`; the count then stays >= 0). A packed slot is updated with one
 // 64-bit atomic: the count lives in the low word and never carries or borrows
-// into the label. If no slot is free, or a label to decrement is missing
-// (only possible after a lost update), the rebuild flag is raised.
+// into the label. A build (BUILD) probes the whole table, which at most two
+// thirds of its slots can fill; an update gives up after HUB_PROBE_MAX probes
+// or when a label to decrement is missing, and then flags the hub.
+template <bool BUILD>
 __device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
+  if (!BUILD && s.hub_rb[h]) return;
   const int64_t base = s.hub_tab[h];
   const int64_t cap = s.hub_tab[h + 1] - base;
+  const int64_t lim = BUILD ? cap : (cap < HUB_PROBE_MAX ? cap : HUB_PROBE_MAX);
   int64_t slot = (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
+  bool claimed = false;
   if (!s.hub_wide) {
     unsigned long long* words = s.hub_slot + base;
-    for (int64_t probe = 0; probe < cap; ++probe) {
+    for (int64_t probe = 0; probe < lim; ++probe) {
       unsigned long long cur = words[slot];
       if (cur == SLOT_EMPTY) {
         if (w <= 0) break;
         cur = atomicCAS(&words[slot], SLOT_EMPTY,
                         ((unsigned long long)(uint32_t)label << 32) | (unsigned long long)(uint32_t)w);
-        if (cur == SLOT_EMPTY) return;
+        if (cur == SLOT_EMPTY) {
+          claimed = true;
+          break;
+        }
       }
       if ((int32_t)(cur >> 32) == label) {
         atomicAdd(&words[slot], (unsigned long long)w);
@@ -259,21 +305,29 @@ __device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_
     }
   } else {
     unsigned long long* words = s.hub_slot + 2 * base;  // (label, count) pairs
-    for (int64_t probe = 0; probe < cap; ++probe) {
+    for (int64_t probe = 0; probe < lim; ++probe) {
       unsigned long long cur = words[2 * slot];
       if (cur == SLOT_EMPTY) {
         if (w <= 0) break;
         cur = atomicCAS(&words[2 * slot], SLOT_EMPTY, (unsigned long long)(uint32_t)label);
-        if (cur == SLOT_EMPTY) cur = (uint32_t)label;
+        if (cur == SLOT_EMPTY) {
+          claimed = true;
+          cur = (uint32_t)label;
+        }
       }
       if ((int32_t)(uint32_t)cur == label) {
         atomicAdd(&words[2 * slot + 1], (unsigned long long)w);
-        return;
+        if (!claimed) return;
+        break;
       }
       slot = slot + 1 == cap ? 0 : slot + 1;
     }
   }
-  atomicExch(s.hub_build, 1);  // rebuild before the next scan
+  if (claimed) {
+    const int32_t used = atomicAdd(&s.hub_used[h], 1) + 1;
+    if (BUILD || (int64_t)used * 8 <= cap * 7) return;
+  }
+  hub_flag_rebuild(s, h);
 }
 
 // Read slot i of a hub table at `base`: (label or -1 if empty, count).
@@ -296,17 +350,18 @@ __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u,
                                                     int64_t w) {
   if (!((__ldg(&s.hub_bits[u >> 5]) >> (u & 31)) & 1u)) return;
   const int32_t h = s.hub_idx[u];
-  hub_hist_add(s, h, A, -w);
-  hub_hist_add(s, h, c, w);
+  hub_hist_add<false>(s, h, A, -w);
+  hub_hist_add<false>(s, h, c, w);
 }
 
 // ------------------------------------------------------------------ tiles
 
 // TILE lanes per vertex, one arc per lane (degree <= TILE).
 template <int TILE, bool LOUV, class W>
-__global__ void __launch_bounds__(NT) k_scan_tile(ScanCtx s, const int32_t* __restrict__ list,
-                                                  int64_t count, int bin) {
+__global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* __restrict__ list,
+                                                  const unsigned long long* __restrict__ count_p, int bin) {
   typedef typename KeyOf<LOUV>::T K;
+  const int64_t count = (int64_t)*count_p;
   __shared__ int64_t stage[NW][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int sub = lane & (TILE - 1);
@@ -462,32 +517,69 @@ __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_
                                            int gl, int32_t* keys, V* vals, const uint16_t* occ, int nocc,
                                            typename KeyOf<LOUV>::T& bk, int32_t& bc, bool& hc,
                                            int64_t& kc, int64_t& ncand) {
-  for (int j = gl; j < nocc; j += GROUP) {
-    const int slot = occ[j];
-    const int32_t c = keys[slot];
-    const int64_t k = (int64_t)vals[slot];
-    keys[slot] = EMPTY;
-    vals[slot] = 0;
-    ++ncand;
-    if (c == cur) {
-      hc = true;
-      kc = k;
-      if (LOUV) continue;
+  constexpr int EB = 2;  // candidates per thread per batch: the Sigma_tot gathers go out together
+  for (int j0 = gl; j0 < nocc; j0 += EB * GROUP) {
+    int32_t c[EB];
+    int64_t k[EB], sg[EB];
+#pragma unroll
+    for (int q = 0; q < EB; ++q) {
+      const int j = j0 + q * GROUP;
+      c[q] = -1;
+      k[q] = 0;
+      if (j < nocc) {
+        const int slot = occ[j];
+        c[q] = keys[slot];
+        k[q] = (int64_t)vals[slot];
+        keys[slot] = EMPTY;
+        vals[slot] = 0;
+      }
     }
-    const typename KeyOf<LOUV>::T key = cand_key<LOUV>(s, c, k, dv, vol);
-    if (better(key, c, bk, bc)) {
-      bk = key;
-      bc = c;
+#pragma unroll
+    for (int q = 0; q < EB; ++q) sg[q] = (LOUV && c[q] >= 0) ? s.sigma[c[q]] : 0;
+#pragma unroll
+    for (int q = 0; q < EB; ++q) {
+      if (c[q] < 0) continue;
+      ++ncand;
+      if (c[q] == cur) {
+        hc = true;
+        kc = k[q];
+        if (LOUV) continue;
+      }
+      const typename KeyOf<LOUV>::T key = cand_key_sg<LOUV>(sg[q], k[q], dv, vol);
+      if (better(key, c[q], bk, bc)) {
+        bk = key;
+        bc = c[q];
+      }
     }
   }
 }
 
+// What a scan needs of a vertex before reading its row.
+struct VHdr {
+  int64_t beg, end, dv, vol;
+  int32_t cur;
+  bool act;
+};
+
+template <bool LOUV>
+__device__ __forceinline__ VHdr load_hdr(const ScanCtx& s, int32_t v, bool valid) {
+  VHdr h;
+  h.act = valid && is_active(s, v);
+  h.beg = valid ? s.off[v] : 0;
+  h.end = valid ? s.off[v + 1] : 0;
+  h.cur = valid ? s.C[v] : 0;
+  h.dv = (LOUV && valid) ? s.degw[v] : 0;
+  h.vol = (LOUV && valid) ? vol_of(s, v) : 0;
+  return h;
+}
+
 // GROUP threads per vertex (a warp, or a named-barrier group of 128 or 512
 // threads), each group with its own CAP-slot shared-memory table.
-template <bool LOUV, class W, class V, int GROUP, int NTB, int CAP, int BIN>
-__global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __restrict__ list,
-                                                    int64_t count) {
+template <bool LOUV, class W, class V, int GROUP, int NTB, int CAP, int BIN, bool PF>
+__global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5) : 2)
+    k_scan_group(ScanCtx s, const int32_t* __restrict__ list, const unsigned long long* __restrict__ count_p) {
   typedef typename KeyOf<LOUV>::T K;
+  const int64_t count = (int64_t)*count_p;
   constexpr int GPB = NTB / GROUP;  // groups per CTA
   constexpr int WPG = GROUP / 32;   // warps per group
   extern __shared__ __align__(16) unsigned char smem[];
@@ -511,17 +603,40 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
   if (gl == 0) occ_n[gid] = 0;
   group_sync<GROUP, NTB>(gid);
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
-  for (int64_t i = (int64_t)blockIdx.x * GPB + gid; i < count; i += (int64_t)gridDim.x * GPB) {
-    const int32_t v = list[i];
-    if (!is_active(s, v)) continue;  // uniform within the group
-    const int64_t beg = s.off[v], end = s.off[v + 1];
+  // Software pipeline over the group's vertices: while vertex i is processed,
+  // the header of vertex i + stride (activity, row bounds, label, deg_w) and
+  // the list entry of vertex i + 2 stride are already in flight.
+  const int64_t stride = (int64_t)gridDim.x * GPB;
+  int64_t i = (int64_t)blockIdx.x * GPB + gid;
+  int32_t v_nx = 0, v_nn = 0;
+  VHdr h_nx{};
+  if constexpr (PF) {
+    v_nx = i < count ? list[i] : 0;
+    h_nx = load_hdr<LOUV>(s, v_nx, i < count);
+    v_nn = i + stride < count ? list[i + stride] : 0;
+  }
+  for (; i < count; i += stride) {
+    int32_t v;
+    VHdr h;
+    if constexpr (PF) {
+      v = v_nx;
+      h = h_nx;
+      v_nx = v_nn;
+      h_nx = load_hdr<LOUV>(s, v_nx, i + stride < count);
+      v_nn = i + 2 * stride < count ? list[i + 2 * stride] : 0;
+    } else {
+      v = list[i];
+      h = load_hdr<LOUV>(s, v, true);
+    }
+    if (!h.act) continue;  // uniform within the group
+    const int64_t beg = h.beg, end = h.end;
     const int64_t d = end - beg;
     const unsigned lg = ceil_log2(2 * d);
-    const int32_t cur = s.C[v];
+    const int32_t cur = h.cur;
     group_insert<W, V, GROUP>(s, v, beg, end, gl, keys, vals, occ, &occ_n[gid], lg, stage);
     group_sync<GROUP, NTB>(gid);
-    const int64_t dv = LOUV ? s.degw[v] : 0;
-    const int64_t volv = LOUV ? vol_of(s, v) : 0;
+    const int64_t dv = h.dv;
+    const int64_t volv = h.vol;
     const int nocc = occ_n[gid];
     K bk = K(0);
     int32_t bc = NOCAND;
@@ -577,17 +692,30 @@ __global__ void __launch_bounds__(NTB) k_scan_group(ScanCtx s, const int32_t* __
 // committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
 // therefore reads its distinct labels instead of its whole row.
 
-// Clear every hub histogram when a rebuild is due (flag set).
-__global__ void __launch_bounds__(NT) k_hub_clear(ScanCtx s, int64_t slots) {
-  if (!*(volatile int32_t*)s.hub_build) return;
-  const int64_t stride = (int64_t)gridDim.x * NT;
-  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < slots; i += stride) {
-    if (!s.hub_wide) {
-      s.hub_slot[i] = SLOT_EMPTY;
-    } else {
-      s.hub_slot[2 * i] = SLOT_EMPTY;
-      s.hub_slot[2 * i + 1] = 0;
+// Start of a round, a CTA per hub flagged in the previous round (every hub in
+// round 0): clear its table and queue its build items.
+__global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
+  __shared__ unsigned long long pos;
+  const int64_t nf = (int64_t)*(volatile const unsigned long long*)s.hub_fcnt_r;
+  for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
+    const int32_t h = s.hub_flist_r[q];
+    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
+    for (int64_t i = threadIdx.x; i < cap; i += NT) {
+      if (!s.hub_wide) {
+        s.hub_slot[base + i] = SLOT_EMPTY;
+      } else {
+        s.hub_slot[2 * (base + i)] = SLOT_EMPTY;
+        s.hub_slot[2 * (base + i) + 1] = 0;
+      }
     }
+    const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
+    if (threadIdx.x == 0) {
+      s.hub_used[h] = 0;
+      pos = atomicAdd(&s.hub_lcnt[0], (unsigned long long)ni);
+    }
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < ni; j += NT) s.hub_blist[pos + j] = (int32_t)(i0 + j);
+    __syncthreads();
   }
 }
 
@@ -595,11 +723,10 @@ constexpr int HUB_NT = 512;
 constexpr int HUB_CAP = 2 * HUB_CHUNK;
 static_assert(HUB_CAP == 8192, "hub chunk table");
 
-// Rebuild (flag set): every item is one HUB_CHUNK-arc chunk of a hub row,
-// combined in a shared-memory table, then added to the hub's histogram.
+// Rebuild of the queued hubs: every item is one HUB_CHUNK-arc chunk of a hub
+// row, combined in a shared-memory table, then added to the hub's histogram.
 template <class W, class V>
 __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
-  if (!*(volatile int32_t*)s.hub_build) return;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int occ_n;
   V* vals = (V*)smem;
@@ -612,7 +739,9 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
   }
   if (threadIdx.x == 0) occ_n = 0;
   __syncthreads();
-  for (int64_t it = blockIdx.x; it < s.n_items; it += gridDim.x) {
+  const int64_t nb = (int64_t)*(volatile unsigned long long*)&s.hub_lcnt[0];
+  for (int64_t q = blockIdx.x; q < nb; q += gridDim.x) {
+    const int32_t it = s.hub_blist[q];
     const int32_t h = s.hub_item_hub[it];
     const int32_t v = s.hub_list[h];
     const int64_t a0 = s.hub_item_arc[it];
@@ -627,7 +756,7 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
       const int64_t k = (int64_t)vals[slot];
       keys[slot] = EMPTY;
       vals[slot] = 0;
-      hub_hist_add(s, h, c, k);
+      hub_hist_add<true>(s, h, c, k);
     }
     __syncthreads();
     if (threadIdx.x == 0) occ_n = 0;
@@ -645,9 +774,18 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   __shared__ int32_t red_c[NW];
   __shared__ int s_last;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *s.hub_build = 0;  // the build (if any) is done
+  {
+    const int64_t nb = (int64_t)*(volatile unsigned long long*)&s.hub_lcnt[0];
+    for (int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x; q < nb; q += (int64_t)gridDim.x * NT) {
+      const int32_t it = s.hub_blist[q];
+      const int32_t h = s.hub_item_hub[it];
+      if (s.hub_item_first[h] == it) s.hub_rb[h] = 0;
+    }
+  }
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
-  for (int64_t it = blockIdx.x; it < s.n_ev_items; it += gridDim.x) {
+  const int64_t n_ev = (int64_t)*s.ev_cnt;
+  for (int64_t q = blockIdx.x; q < n_ev; q += gridDim.x) {
+    const int64_t it = s.ev_list ? s.ev_list[q] : q;
     const int32_t h = s.hub_ev_hub[it];
     const int32_t v = s.hub_list[h];
     if (!is_active(s, v)) continue;  // uniform within the CTA
@@ -660,18 +798,21 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
     const int64_t e1 = e0 + HUB_SLICE < cap ? e0 + HUB_SLICE : cap;
     K bk = K(0);
     int32_t bc = NOCAND;
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += 4 * NT) {
-      int32_t c[4];
-      int64_t k[4];
+    constexpr int HB = 6;  // slots per thread per batch: all loads, then all gathers, in flight together
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += HB * NT) {
+      int32_t c[HB];
+      int64_t k[HB], sg[HB];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {  // issue the four slot loads first
+      for (int j = 0; j < HB; ++j) {
         const int64_t x = e + (int64_t)j * NT;
         c[j] = -1;
         k[j] = 0;
         if (x < e1) hub_slot_read(s, base, x, c[j], k[j]);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < HB; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? s.sigma[c[j]] : 0;
+#pragma unroll
+      for (int j = 0; j < HB; ++j) {
         if (c[j] < 0 || k[j] == 0) continue;  // unused entry, or a label that left
         ++n_cand;
         if (c[j] == cur) {
@@ -679,7 +820,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
           s.hub_hascur[h] = 1;
           if (LOUV) continue;
         }
-        const K key = cand_key<LOUV>(s, c[j], k[j], dv, volv);
+        const K key = cand_key_sg<LOUV>(sg[j], k[j], dv, volv);
         if (better(key, c[j], bk, bc)) {
           bk = key;
           bc = c[j];
@@ -729,6 +870,9 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
         s.hub_mv[3 * h] = 1;
         s.hub_mv[3 * h + 1] = cur;
         s.hub_mv[3 * h + 2] = target;
+        const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
+        const unsigned long long pos = atomicAdd(&s.hub_lcnt[1], (unsigned long long)ni);
+        for (int64_t j = 0; j < ni; ++j) s.hub_mlist[pos + j] = (int32_t)(i0 + j);
       }
       ++n_act;
       n_arcs += s.off[v + 1] - s.off[v];
@@ -741,37 +885,110 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
 }
 
+// ------------------------------------------------------------------ frontier
+
+struct BinBounds {
+  int64_t b[NBINS + 1];
+};
+
+// The active vertices of a round into per-bin lists (bin b at act + b.b[b],
+// order arbitrary; the scans do not depend on it), and the evaluate items of
+// the active hubs. Whole warps iterate together for the match.
+__global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __restrict__ bin_list, BinBounds bb,
+                                                int32_t* __restrict__ act, unsigned long long* __restrict__ cnt,
+                                                int32_t* __restrict__ ev) {
+  const int lane = threadIdx.x & 31;
+  const int64_t total = bb.b[NBINS];
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t base = (int64_t)blockIdx.x * NT + (threadIdx.x & ~31); base < total; base += stride) {
+    const int64_t i = base + lane;
+    const bool valid = i < total;
+    const int32_t v = valid ? bin_list[i] : 0;
+    int bin = -1;
+    if (valid && is_active(s, v)) {
+      bin = 0;
+      while (i >= bb.b[bin + 1]) ++bin;
+    }
+    if (bin == B_HUB) {
+      const int32_t h = s.hub_idx[v];
+      const int64_t e0 = s.hub_ev_first[h], ne = s.hub_ev_first[h + 1] - e0;
+      const unsigned long long p = atomicAdd(&cnt[NBINS], (unsigned long long)ne);
+      for (int64_t j = 0; j < ne; ++j) ev[p + j] = (int32_t)(e0 + j);
+    }
+    const int key = bin != B_HUB ? bin : -1;
+    const unsigned peers = __match_any_sync(FULL, key);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long p0 = 0;
+    if (key >= 0 && lane == leader) p0 = atomicAdd(&cnt[key], (unsigned long long)__popc(peers));
+    p0 = __shfl_sync(FULL, p0, leader);
+    if (key >= 0) act[bb.b[key] + (int64_t)p0 + __popc(peers & ((1u << lane) - 1u))] = v;
+  }
+}
+
 // ------------------------------------------------------------------ apply
 
 // Thread per committed move (vertex v: A -> c): the new label, and Sigma_tot
 // and community sizes for Louvain. (The scan kernels flag the neighbours of
 // their committed vertices and update neighbouring hub histograms; moved hubs
 // are handled by k_hub_mark.)
+// Add `d` to sigma[key] and `one` to csize[key] for every lane with key >= 0,
+// one atomic pair per distinct key of the warp: popular target communities
+// would otherwise serialise on one address.
+__device__ __forceinline__ void warp_add_community(int64_t* sigma, int32_t* csize, int32_t key, int64_t d,
+                                                   int32_t one, int64_t* stage) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(FULL, key);
+  stage[lane] = d;
+  __syncwarp();
+  if (key >= 0 && (__ffs(peers) - 1) == lane) {
+    int64_t sum = 0;
+    unsigned m = peers;
+    while (m) {
+      sum += stage[__ffs(m) - 1];
+      m &= m - 1;
+    }
+    atomicAdd((unsigned long long*)&sigma[key], (unsigned long long)sum);
+    atomicAdd(&csize[key], one * __popc(peers));
+  }
+  __syncwarp();
+}
+
 template <bool LOUV>
 __global__ void __launch_bounds__(NT) k_apply_state(ScanCtx s, int64_t nmoves, int64_t* sigma,
                                                     int32_t* csize, int32_t* C) {
+  __shared__ int64_t stage[NW][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * NT;
-  for (int64_t m = (int64_t)blockIdx.x * NT + threadIdx.x; m < nmoves; m += stride) {
-    const int32_t v = s.mv_v[m], c = s.mv_c[m];
-    if (LOUV) {
-      const int32_t A = s.mv_a[m];
-      const int64_t d = s.degw[v];
-      atomicAdd((unsigned long long*)&sigma[A], (unsigned long long)(-d));
-      atomicAdd((unsigned long long*)&sigma[c], (unsigned long long)d);
-      atomicSub(&csize[A], 1);
-      atomicAdd(&csize[c], 1);
+  // whole warps iterate together (the match needs every lane)
+  for (int64_t base = (int64_t)blockIdx.x * NT + wid * 32; base < nmoves; base += stride) {
+    const int64_t m = base + lane;
+    const bool ok = m < nmoves;
+    int32_t v = 0, c = -1, A = -1;
+    if (ok) {
+      v = s.mv_v[m];
+      c = s.mv_c[m];
+      C[v] = c;
     }
-    C[v] = c;
+    if (LOUV) {
+      int64_t d = 0;
+      if (ok) {
+        A = s.mv_a[m];
+        d = s.degw[v];
+      }
+      warp_add_community(sigma, csize, c, d, 1, stage[wid]);
+      warp_add_community(sigma, csize, A, -d, -1, stage[wid]);
+    }
   }
 }
 
-// Moved hubs, one item per HUB_CHUNK arcs: flag the neighbours and update the
-// histograms of neighbouring hubs.
+// Moved hubs, one queued item per HUB_CHUNK arcs: flag the neighbours and
+// update the histograms of neighbouring hubs.
 template <class W>
 __global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
-  for (int64_t it = blockIdx.x; it < s.n_items; it += gridDim.x) {
+  const int64_t nm = (int64_t)*(volatile unsigned long long*)&s.hub_lcnt[1];
+  for (int64_t q = blockIdx.x; q < nm; q += gridDim.x) {
+    const int32_t it = s.hub_mlist[q];
     const int32_t h = s.hub_item_hub[it];
-    if (!s.hub_mv[3 * h]) continue;
     const int32_t A = s.hub_mv[3 * h + 1], c = s.hub_mv[3 * h + 2];
     const int32_t v = s.hub_list[h];
     const int64_t a0 = s.hub_item_arc[it];
@@ -784,6 +1001,16 @@ __global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
       hub_neighbour_moved(s, u, A, c, W::get(s.w, e));
     }
   }
+}
+
+__global__ void k_fill_i32(int32_t* a, int64_t n, int32_t x) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = x;
+}
+
+__global__ void k_iota_i32(int32_t* a, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = (int32_t)i;
 }
 
 __global__ void k_init_singletons(int32_t* C, int64_t* sigma, int32_t* csize,
@@ -812,6 +1039,29 @@ unsigned grid_cap(int64_t blocks, int64_t cap = 152 * 16) {
   return (unsigned)(blocks < cap ? blocks : cap);
 }
 
+// CTAs of `kernel` resident on the device at once (occupancy x SMs), cached
+// per kernel. Scan grids are capped to this: a grid-stride loop over one wave
+// has no partly filled second wave.
+int resident_ctas(const void* kernel, int nt, size_t smem) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(kernel);
+  if (it != cache.end()) return it->second;
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, smem);
+  const int r = std::max(1, per) * std::max(1, sms);
+  cache[kernel] = r;
+  return r;
+}
+
+template <class KERN>
+unsigned wave_grid(KERN kernel, int nt, size_t smem, int64_t want) {
+  return grid_cap(want, resident_ctas((const void*)kernel, nt, smem));
+}
+
 // Group-kernel configurations: (GROUP threads per vertex, CTA size, table slots).
 template <class V> constexpr size_t group_smem(int gpb, int cap, int ntb) {
   return (size_t)gpb * cap * (sizeof(V) + 4) + (size_t)(ntb / 32) * 32 * 8 + (size_t)gpb * cap * 2;
@@ -824,9 +1074,9 @@ template <bool LOUV, class W, class V>
 int set_smem_attrs() {
   static std::atomic<bool> done{false};  // idempotent; threads may race here
   if (done) return CD_OK;
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
@@ -844,17 +1094,19 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
 }
 
 template <bool LOUV, class W, class V>
-int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
+int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned long long* counts,
+                 std::vector<std::pair<size_t, int>>& marks) {
   int rc = set_smem_attrs<LOUV, W, V>();
   if (rc) return rc;
   cudaStream_t st = g->stream;
   auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
-  auto lst = [&](int b) { return g->bin_list + g->bin_start[b]; };
+  auto lst = [&](int b) { return lists + g->bin_start[b]; };
+  auto dcnt = [&](int b) { return counts + b; };
   auto mark = [&](int b) { marks.push_back({g->pending.size() - 1, b}); };
   if (cnt(B_HUB) > 0) {
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
-      CD_LAUNCH(k_hub_clear<<<grid_cap((g->hub_slots + NT - 1) / NT, 152 * 8), NT, 0, st>>>(s, g->hub_slots));
+      CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 8), NT, 0, st>>>(s));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
@@ -867,50 +1119,56 @@ int launch_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& m
   if (cnt(B_BLK1) > 0) {
     {
       KTimer t(g, K_SCAN_BLK128);
-      CD_LAUNCH((k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1>
-                 <<<grid_cap((cnt(B_BLK1) + 3) / 4, 152 * 3), 512, blk1_smem<V>(), st>>>(s, lst(B_BLK1),
-                                                                                        cnt(B_BLK1))));
+      auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>;
+      CD_LAUNCH((kern<<<grid_cap((cnt(B_BLK1) + 3) / 4, BLK_WAVES * resident_ctas((const void*)kern, 512,
+                                                                                blk1_smem<V>())),
+                        512, blk1_smem<V>(), st>>>(
+          s, lst(B_BLK1), dcnt(B_BLK1))));
     }
     if (g->timing) mark(B_BLK1);
   }
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP);
-      CD_LAUNCH((k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP>
-                 <<<grid_cap((cnt(B_WARP) + NW - 1) / NW, 152 * 6), 256, warp_smem<V>(), st>>>(s, lst(B_WARP),
-                                                                                              cnt(B_WARP))));
+      auto kern = k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true>;
+      CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + NW - 1) / NW), 256, warp_smem<V>(),
+                        st>>>(s, lst(B_WARP), dcnt(B_WARP))));
     }
     if (g->timing) mark(B_WARP);
   }
   if (cnt(B_T32) > 0) {
     {
       KTimer t(g, K_SCAN_T32);
-      CD_LAUNCH(k_scan_tile<32, LOUV, W><<<grid_cap((cnt(B_T32) + NW - 1) / NW), NT, 0, st>>>(
-          s, lst(B_T32), cnt(B_T32), B_T32));
+      auto kern = k_scan_tile<32, LOUV, W>;
+      CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T32) + NW - 1) / (NW)), NT, 0, st>>>(
+          s, lst(B_T32), dcnt(B_T32), B_T32));
     }
     if (g->timing) mark(B_T32);
   }
   if (cnt(B_T16) > 0) {
     {
       KTimer t(g, K_SCAN_T16);
-      CD_LAUNCH(k_scan_tile<16, LOUV, W><<<grid_cap((cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
-          s, lst(B_T16), cnt(B_T16), B_T16));
+      auto kern = k_scan_tile<16, LOUV, W>;
+      CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
+          s, lst(B_T16), dcnt(B_T16), B_T16));
     }
     if (g->timing) mark(B_T16);
   }
   if (cnt(B_T8) > 0) {
     {
       KTimer t(g, K_SCAN_T8);
-      CD_LAUNCH(k_scan_tile<8, LOUV, W><<<grid_cap((cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
-          s, lst(B_T8), cnt(B_T8), B_T8));
+      auto kern = k_scan_tile<8, LOUV, W>;
+      CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
+          s, lst(B_T8), dcnt(B_T8), B_T8));
     }
     if (g->timing) mark(B_T8);
   }
   if (cnt(B_T4) > 0) {
     {
       KTimer t(g, K_SCAN_T4);
-      CD_LAUNCH(k_scan_tile<4, LOUV, W><<<grid_cap((cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
-          s, lst(B_T4), cnt(B_T4), B_T4));
+      auto kern = k_scan_tile<4, LOUV, W>;
+      CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
+          s, lst(B_T4), dcnt(B_T4), B_T4));
     }
     if (g->timing) mark(B_T4);
   }
@@ -932,9 +1190,12 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     CD_CHECK(cudaMemsetAsync(g->gfrozen, 0, g->nb, st));
   }
   int rc = CD_OK;
-  if (g->nhubs > 0) {  // histograms are built from the starting labels in round 0
-    const int32_t one = 1;
-    CD_CHECK(cudaMemcpyAsync(g->hub_build, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (g->nhubs > 0) {  // every histogram is built from the starting labels in round 0
+    CD_LAUNCH(k_fill_i32<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(g->hub_rb, g->nhubs, 1));
+    CD_LAUNCH(k_iota_i32<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(g->hub_flist + g->nhubs, g->nhubs));
+    const unsigned long long nh = (unsigned long long)g->nhubs;
+    CD_CHECK(cudaMemcpyAsync(g->hub_fcnt + 1, &nh, sizeof(nh), cudaMemcpyHostToDevice, st));
+    CD_CHECK(cudaStreamSynchronize(st));  // nh lives on this stack frame
   }
   uint8_t* fcur = g->flag[0];
   uint8_t* fnxt = g->flag[1];
@@ -950,7 +1211,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
     if (per_graph_stop) CD_CHECK(cudaMemsetAsync(g->gcnt, 0, g->nb * sizeof(int64_t), st));
     if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, n, st));
-    if (g->nhubs > 0) CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
+    if (g->nhubs > 0) {
+      CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
+      CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
+      CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
+    }
     ScanCtx s;
     s.off = g->off;
     s.cols = g->cols;
@@ -990,7 +1255,16 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.hub_hascur = g->hub_hascur;
     s.hub_done = g->hub_done;
     s.hub_mv = g->hub_mv;
-    s.hub_build = g->hub_build;
+    s.hub_rb = g->hub_rb;
+    s.hub_used = g->hub_used;
+    s.hub_item_first = g->hub_item_first;
+    s.hub_blist = g->hub_blist;
+    s.hub_mlist = g->hub_mlist;
+    s.hub_lcnt = g->hub_lcnt;
+    s.hub_flist_w = g->hub_flist ? g->hub_flist + (r & 1) * g->nhubs : nullptr;
+    s.hub_fcnt_w = g->hub_fcnt ? g->hub_fcnt + (r & 1) : nullptr;
+    s.hub_flist_r = g->hub_flist ? g->hub_flist + ((r + 1) & 1) * g->nhubs : nullptr;
+    s.hub_fcnt_r = g->hub_fcnt ? g->hub_fcnt + ((r + 1) & 1) : nullptr;
     s.n_items = g->hub_items;
     s.nhubs = g->nhubs;
     s.n_ev_items = g->hub_eval_items;
@@ -999,22 +1273,40 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.gvol = o.batched ? g->gvol : nullptr;
     s.gfrozen = o.batched ? g->gfrozen : nullptr;
     s.gcnt = per_graph_stop ? (unsigned long long*)g->gcnt : nullptr;
+    // the round's work lists: every listed vertex in round 0 (or without a
+    // frontier), else the active ones, compacted
+    const int32_t* lists = g->bin_list;
+    const unsigned long long* counts = g->full_cnt;
+    s.ev_list = nullptr;
+    s.ev_cnt = g->full_cnt + NBINS;
+    if (o.use_frontier && r > 0 && g->bin_start[NBINS] > 0) {
+      KTimer t(g, K_FRONTIER, (double)g->bin_start[NBINS] * (4 + 1 + 4));
+      CD_CHECK(cudaMemsetAsync(g->act_cnt, 0, (NBINS + 1) * sizeof(unsigned long long), st));
+      BinBounds bb;
+      for (int b = 0; b <= NBINS; ++b) bb.b[b] = g->bin_start[b];
+      CD_LAUNCH(k_compact<<<wave_grid(k_compact, NT, 0, (g->bin_start[NBINS] + NT - 1) / NT), NT, 0, st>>>(
+          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev));
+      lists = g->act_list;
+      counts = g->act_cnt;
+      s.ev_list = g->act_ev;
+      s.ev_cnt = g->act_cnt + NBINS;
+    }
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
     if (louv) {
-      if (g->wkind == W_UNIT) rc = v32 ? launch_round<true, WUnit, uint32_t>(g, s, marks)
-                                       : launch_round<true, WUnit, unsigned long long>(g, s, marks);
-      else if (g->wkind == W_I32) rc = v32 ? launch_round<true, WI32, uint32_t>(g, s, marks)
-                                           : launch_round<true, WI32, unsigned long long>(g, s, marks);
-      else rc = v32 ? launch_round<true, WI64, uint32_t>(g, s, marks)
-                    : launch_round<true, WI64, unsigned long long>(g, s, marks);
+      if (g->wkind == W_UNIT) rc = v32 ? launch_round<true, WUnit, uint32_t>(g, s, lists, counts, marks)
+                                       : launch_round<true, WUnit, unsigned long long>(g, s, lists, counts, marks);
+      else if (g->wkind == W_I32) rc = v32 ? launch_round<true, WI32, uint32_t>(g, s, lists, counts, marks)
+                                           : launch_round<true, WI32, unsigned long long>(g, s, lists, counts, marks);
+      else rc = v32 ? launch_round<true, WI64, uint32_t>(g, s, lists, counts, marks)
+                    : launch_round<true, WI64, unsigned long long>(g, s, lists, counts, marks);
     } else {
-      if (g->wkind == W_UNIT) rc = v32 ? launch_round<false, WUnit, uint32_t>(g, s, marks)
-                                       : launch_round<false, WUnit, unsigned long long>(g, s, marks);
-      else if (g->wkind == W_I32) rc = v32 ? launch_round<false, WI32, uint32_t>(g, s, marks)
-                                           : launch_round<false, WI32, unsigned long long>(g, s, marks);
-      else rc = v32 ? launch_round<false, WI64, uint32_t>(g, s, marks)
-                    : launch_round<false, WI64, unsigned long long>(g, s, marks);
+      if (g->wkind == W_UNIT) rc = v32 ? launch_round<false, WUnit, uint32_t>(g, s, lists, counts, marks)
+                                       : launch_round<false, WUnit, unsigned long long>(g, s, lists, counts, marks);
+      else if (g->wkind == W_I32) rc = v32 ? launch_round<false, WI32, uint32_t>(g, s, lists, counts, marks)
+                                           : launch_round<false, WI32, unsigned long long>(g, s, lists, counts, marks);
+      else rc = v32 ? launch_round<false, WI64, uint32_t>(g, s, lists, counts, marks)
+                    : launch_round<false, WI64, unsigned long long>(g, s, lists, counts, marks);
     }
     if (rc) break;
     if (g->timing) cudaEventRecord(ev[1], st);
@@ -1043,13 +1335,16 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       g->pending_bytes[mk.first] = bytes;
     }
     if (moves > 0) {
-      KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
-      const unsigned gt = grid_cap((moves + NT - 1) / NT);
-      if (louv)
-        CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
-      else
-        CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+      {
+        KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
+        const unsigned gt = grid_cap((moves + NT - 1) / NT);
+        if (louv)
+          CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+        else
+          CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+      }
       if (g->nhubs > 0) {
+        KTimer t(g, K_HUB_MARK);
         const unsigned gh = grid_cap(g->hub_items, 152 * 8);
         if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, st>>>(s));
         else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, st>>>(s));
