@@ -26,6 +26,7 @@ constexpr int BLOCK_MAX = 1024;  // largest degree scanned through shared-memory
 // (group vs hub histogram) may be lowered below these capacities (autotuner).
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
 constexpr int HUB_SLICE = 4096;  // histogram slots per hub evaluate item
+constexpr int HUB_SMALL = 8192;  // hubs of at most this many slots are evaluated by one warp
 constexpr int COL_PAD = 4;       // column arrays carry 4 spare entries for 16-byte loads
 
 // Weight kinds of the device CSR.
@@ -81,9 +82,13 @@ struct cd_graph {
   int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
   // frontier: the active vertices of a round, bin b at act_list + bin_start[b]
   int32_t* act_list = nullptr;
-  unsigned long long* act_cnt = nullptr;   // NBINS+1: active per bin, then active hub evaluate items
-  unsigned long long* full_cnt = nullptr;  // NBINS+1: every listed vertex per bin, then every item
-  int32_t* act_ev = nullptr;               // hub_eval_items: evaluate items of the active hubs
+  unsigned long long* act_cnt = nullptr;   // NBINS+2: active per bin, large-hub items, small hubs
+  unsigned long long* full_cnt = nullptr;  // NBINS+2: the same for every listed vertex
+  int32_t* act_ev = nullptr;               // evaluate items of the active large hubs
+  int32_t* act_small = nullptr;            // active small hubs
+  int32_t* hub_big_items = nullptr;        // every evaluate item of a large hub
+  int32_t* hub_small = nullptr;            // every small hub
+  int64_t n_small_hubs = 0, n_big_items = 0;
   // hubs (degree > BLOCK_MAX): one persistent label histogram per hub, kept in
   // step with the labels by the moves of its neighbours: an open-addressing
   // table of cap_h = 1.5 deg + 64 slots in [hub_tab[h], hub_tab[h+1]). A slot

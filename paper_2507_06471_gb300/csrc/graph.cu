@@ -305,7 +305,8 @@ int read_status(cd_graph* g) {
 void free_arrays(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
-                g->act_list,     g->act_cnt,       g->full_cnt,     g->act_ev,
+                g->act_list,     g->act_cnt,       g->full_cnt,     g->act_ev,       g->act_small,
+                g->hub_big_items, g->hub_small,
                 g->hub_idx,      g->hub_bits,      g->hub_tab,       g->hub_slot,
                 g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
@@ -322,6 +323,7 @@ void free_arrays(cd_graph* g) {
 void free_bins(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->bin_list,     g->act_list,    g->act_cnt,      g->full_cnt,  g->act_ev,
+                g->act_small,    g->hub_big_items, g->hub_small,
                 g->hub_idx,      g->hub_bits,     g->hub_tab,   g->hub_slot,
                 g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
@@ -334,6 +336,10 @@ void free_bins(cd_graph* g) {
   g->act_cnt = nullptr;
   g->full_cnt = nullptr;
   g->act_ev = nullptr;
+  g->act_small = nullptr;
+  g->hub_big_items = nullptr;
+  g->hub_small = nullptr;
+  g->n_small_hubs = g->n_big_items = 0;
   g->hub_idx = nullptr;
   g->hub_bits = nullptr;
   g->hub_tab = nullptr;
@@ -392,8 +398,8 @@ int build_bins(cd_graph* g) {
   rc = dev_alloc_t(&g->bin_list, listed, s);
   if (rc) return rc;
   if ((rc = dev_alloc_t(&g->act_list, listed, s))) return rc;
-  if ((rc = dev_alloc_t(&g->act_cnt, NBINS + 1, s))) return rc;
-  if ((rc = dev_alloc_t(&g->full_cnt, NBINS + 1, s))) return rc;
+  if ((rc = dev_alloc_t(&g->act_cnt, NBINS + 2, s))) return rc;
+  if ((rc = dev_alloc_t(&g->full_cnt, NBINS + 2, s))) return rc;
   int64_t* d_base = nullptr;
   unsigned long long* d_cur = nullptr;
   if ((rc = dev_alloc_t(&d_base, NBINS, s))) return rc;
@@ -417,7 +423,7 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaStreamSynchronize(s));
     dev_free(d_rows, s);
     std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0), ev_slot, item_first(nh + 1, 0);
-    std::vector<int32_t> item_hub, ev_hub;
+    std::vector<int32_t> item_hub, ev_hub, small, big_items;
     for (int64_t h = 0; h < nh; ++h) {
       int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
       int64_t cap = deg + deg / 2 + 64;  // live labels <= deg; the rest absorbs labels that come and go
@@ -428,7 +434,9 @@ int build_bins(cd_graph* g) {
         item_arc.push_back(beg + a);
       }
       ev_first[h] = (int64_t)ev_hub.size();
+      if (cap <= HUB_SMALL) small.push_back((int32_t)h);
       for (int64_t e = 0; e < cap; e += HUB_SLICE) {
+        if (cap > HUB_SMALL) big_items.push_back((int32_t)ev_hub.size());
         ev_hub.push_back((int32_t)h);
         ev_slot.push_back(e);
       }
@@ -439,6 +447,15 @@ int build_bins(cd_graph* g) {
     g->hub_items = (int64_t)item_hub.size();
     g->hub_eval_items = (int64_t)ev_hub.size();
     if ((rc = dev_alloc_t(&g->act_ev, g->hub_eval_items, s))) return rc;
+    g->n_small_hubs = (int64_t)small.size();
+    g->n_big_items = (int64_t)big_items.size();
+    if ((rc = dev_alloc_t(&g->act_small, g->n_small_hubs, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_small, g->n_small_hubs, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_big_items, g->n_big_items, s))) return rc;
+    if (!small.empty())
+      CD_CHECK(cudaMemcpyAsync(g->hub_small, small.data(), small.size() * 4, cudaMemcpyHostToDevice, s));
+    if (!big_items.empty())
+      CD_CHECK(cudaMemcpyAsync(g->hub_big_items, big_items.data(), big_items.size() * 4, cudaMemcpyHostToDevice, s));
     if ((rc = dev_alloc_t(&g->hub_idx, g->n, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_bits, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
@@ -483,9 +500,10 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
   }
   {
-    unsigned long long full[NBINS + 1];
+    unsigned long long full[NBINS + 2];
     for (int b = 0; b < NBINS; ++b) full[b] = (unsigned long long)(g->bin_start[b + 1] - g->bin_start[b]);
-    full[NBINS] = (unsigned long long)g->hub_eval_items;
+    full[NBINS] = (unsigned long long)g->n_big_items;
+    full[NBINS + 1] = (unsigned long long)g->n_small_hubs;
     CD_CHECK(cudaMemcpyAsync(g->full_cnt, full, sizeof(full), cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaStreamSynchronize(s));  // `full` lives on this stack frame
   }

@@ -133,8 +133,10 @@ struct ScanCtx {
   int32_t* hub_blist;                // build items of the hubs being rebuilt this round
   int32_t* hub_mlist;                // mark items of the hubs that moved this round
   unsigned long long* hub_lcnt;      // [0] build items, [1] mark items
-  const int32_t* ev_list;            // evaluate items to run this round (null: all of them)
+  const int32_t* ev_list;            // evaluate items (of large hubs) to run this round
   const unsigned long long* ev_cnt;  // their number
+  const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
+  const unsigned long long* small_cnt;
   int64_t n_items, nhubs, n_ev_items;
   // batched mode (gid == nullptr: one graph)
   const int32_t* gid;
@@ -764,6 +766,88 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
   }
 }
 
+// Decision of hub h (one thread): act on it, and queue the mark items of a
+// committed move (the neighbours are flagged and their hub histograms
+// updated by k_hub_mark).
+template <bool LOUV>
+__device__ __forceinline__ void hub_decide(const ScanCtx& s, int32_t h, int32_t v, int32_t cur,
+                                           typename KeyOf<LOUV>::T fk, int32_t fc, bool hc, int64_t kc,
+                                           int64_t volv, int64_t& n_act, int64_t& n_arcs, int64_t& n_def) {
+  const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc, volv);
+  const int def = act_single(s, v, cur, target);
+  n_def += def;
+  if (target != cur && !def) {
+    s.hub_mv[3 * h] = 1;
+    s.hub_mv[3 * h + 1] = cur;
+    s.hub_mv[3 * h + 2] = target;
+    const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
+    const unsigned long long pos = atomicAdd(&s.hub_lcnt[1], (unsigned long long)ni);
+    for (int64_t j = 0; j < ni; ++j) s.hub_mlist[pos + j] = (int32_t)(i0 + j);
+  }
+  ++n_act;
+  n_arcs += s.off[v + 1] - s.off[v];
+}
+
+// A small hub (at most HUB_SMALL slots) is evaluated by one warp: no partial
+// results, no cross-CTA combination.
+template <bool LOUV>
+__global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
+  typedef typename KeyOf<LOUV>::T K;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
+  const int64_t n = (int64_t)*s.small_cnt;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  for (int64_t q = warp; q < n; q += nwarps) {
+    const int32_t h = s.small_list[q];
+    const int32_t v = s.hub_list[h];
+    if (!is_active(s, v)) continue;  // uniform within the warp
+    const int32_t cur = s.C[v];
+    const int64_t dv = LOUV ? s.degw[v] : 0;
+    const int64_t volv = LOUV ? vol_of(s, v) : 0;
+    const int64_t base = s.hub_tab[h];
+    const int64_t cap = s.hub_tab[h + 1] - base;
+    K bk = K(0);
+    int32_t bc = NOCAND;
+    bool hc = false;
+    int64_t kc = 0;
+    constexpr int U = 4;  // slots per lane per batch, then their gathers
+    for (int64_t e = lane; e < cap; e += U * 32) {
+      int32_t c[U];
+      int64_t k[U], sg[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t x = e + (int64_t)j * 32;
+        c[j] = -1;
+        k[j] = 0;
+        if (x < cap) hub_slot_read(s, base, x, c[j], k[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? s.sigma[c[j]] : 0;
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        if (c[j] < 0 || k[j] == 0) continue;
+        ++n_cand;
+        if (c[j] == cur) {
+          hc = true;
+          kc = k[j];
+          if (LOUV) continue;
+        }
+        const K key = cand_key_sg<LOUV>(sg[j], k[j], dv, volv);
+        if (better(key, c[j], bk, bc)) {
+          bk = key;
+          bc = c[j];
+        }
+      }
+    }
+    reduce_best(bk, bc, 32);
+    const unsigned hm = __ballot_sync(FULL, hc);
+    if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
+    if (lane == 0) hub_decide<LOUV>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def);
+  }
+  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
+}
+
 // Every item scans HUB_SLICE histogram entries of one active hub; the last
 // item of a hub to finish combines the partial bests and decides. Entries
 // with weight 0 (labels that left the neighbourhood) are not candidates.
@@ -785,7 +869,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
   const int64_t n_ev = (int64_t)*s.ev_cnt;
   for (int64_t q = blockIdx.x; q < n_ev; q += gridDim.x) {
-    const int64_t it = s.ev_list ? s.ev_list[q] : q;
+    const int64_t it = s.ev_list[q];
     const int32_t h = s.hub_ev_hub[it];
     const int32_t v = s.hub_list[h];
     if (!is_active(s, v)) continue;  // uniform within the CTA
@@ -863,19 +947,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       }
       const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
       const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
-      const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc, volv);
-      const int def = act_single(s, v, cur, target);
-      n_def += def;
-      if (target != cur && !def) {
-        s.hub_mv[3 * h] = 1;
-        s.hub_mv[3 * h + 1] = cur;
-        s.hub_mv[3 * h + 2] = target;
-        const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
-        const unsigned long long pos = atomicAdd(&s.hub_lcnt[1], (unsigned long long)ni);
-        for (int64_t j = 0; j < ni; ++j) s.hub_mlist[pos + j] = (int32_t)(i0 + j);
-      }
-      ++n_act;
-      n_arcs += s.off[v + 1] - s.off[v];
+      hub_decide<LOUV>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def);
       s.hub_done[h] = 0;
       s.hub_cur[h] = 0;
       s.hub_hascur[h] = 0;
@@ -892,11 +964,12 @@ struct BinBounds {
 };
 
 // The active vertices of a round into per-bin lists (bin b at act + b.b[b],
-// order arbitrary; the scans do not depend on it), and the evaluate items of
-// the active hubs. Whole warps iterate together for the match.
+// order arbitrary; the scans do not depend on it); active hubs go to the
+// small-hub list or, for large ones, their evaluate items to the item list.
+// Whole warps iterate together for the match.
 __global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __restrict__ bin_list, BinBounds bb,
                                                 int32_t* __restrict__ act, unsigned long long* __restrict__ cnt,
-                                                int32_t* __restrict__ ev) {
+                                                int32_t* __restrict__ ev, int32_t* __restrict__ small) {
   const int lane = threadIdx.x & 31;
   const int64_t total = bb.b[NBINS];
   const int64_t stride = (int64_t)gridDim.x * NT;
@@ -911,9 +984,13 @@ __global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __rest
     }
     if (bin == B_HUB) {
       const int32_t h = s.hub_idx[v];
-      const int64_t e0 = s.hub_ev_first[h], ne = s.hub_ev_first[h + 1] - e0;
-      const unsigned long long p = atomicAdd(&cnt[NBINS], (unsigned long long)ne);
-      for (int64_t j = 0; j < ne; ++j) ev[p + j] = (int32_t)(e0 + j);
+      if (s.hub_tab[h + 1] - s.hub_tab[h] <= HUB_SMALL) {
+        small[atomicAdd(&cnt[NBINS + 1], 1ull)] = h;
+      } else {
+        const int64_t e0 = s.hub_ev_first[h], ne = s.hub_ev_first[h + 1] - e0;
+        const unsigned long long p = atomicAdd(&cnt[NBINS], (unsigned long long)ne);
+        for (int64_t j = 0; j < ne; ++j) ev[p + j] = (int32_t)(e0 + j);
+      }
     }
     const int key = bin != B_HUB ? bin : -1;
     const unsigned peers = __match_any_sync(FULL, key);
@@ -1112,6 +1189,9 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
     {
       KTimer t(g, K_HUB_EVAL);
+      if (g->n_small_hubs > 0)
+        CD_LAUNCH(k_hub_eval_small<LOUV><<<wave_grid(k_hub_eval_small<LOUV>, NT, 0, (g->n_small_hubs + NW - 1) / NW),
+                                           NT, 0, st>>>(s));
       CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) mark(B_HUB);
@@ -1277,19 +1357,23 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     // frontier), else the active ones, compacted
     const int32_t* lists = g->bin_list;
     const unsigned long long* counts = g->full_cnt;
-    s.ev_list = nullptr;
+    s.ev_list = g->hub_big_items;
     s.ev_cnt = g->full_cnt + NBINS;
+    s.small_list = g->hub_small;
+    s.small_cnt = g->full_cnt + NBINS + 1;
     if (o.use_frontier && r > 0 && g->bin_start[NBINS] > 0) {
       KTimer t(g, K_FRONTIER, (double)g->bin_start[NBINS] * (4 + 1 + 4));
-      CD_CHECK(cudaMemsetAsync(g->act_cnt, 0, (NBINS + 1) * sizeof(unsigned long long), st));
+      CD_CHECK(cudaMemsetAsync(g->act_cnt, 0, (NBINS + 2) * sizeof(unsigned long long), st));
       BinBounds bb;
       for (int b = 0; b <= NBINS; ++b) bb.b[b] = g->bin_start[b];
       CD_LAUNCH(k_compact<<<wave_grid(k_compact, NT, 0, (g->bin_start[NBINS] + NT - 1) / NT), NT, 0, st>>>(
-          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev));
+          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev, g->act_small));
       lists = g->act_list;
       counts = g->act_cnt;
       s.ev_list = g->act_ev;
       s.ev_cnt = g->act_cnt + NBINS;
+      s.small_list = g->act_small;
+      s.small_cnt = g->act_cnt + NBINS + 1;
     }
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
