@@ -61,6 +61,9 @@ typedef struct cd_params {
   int32_t use_frontier;     /* 1 (default): examine only flagged vertices; 0: all, every round */
   int32_t timing;           /* 1: record CUDA-event times per round and per kernel (trace/profile) */
   uint64_t sched_seed;      /* state of the deferral coin's SplitMix64 stream; default 0x5EED5EED */
+  int32_t aggregation;      /* Louvain aggregation: 0 hash-combine per community (default), 1 radix sort
+                               of all arcs; the coarse graphs have the same rows either way */
+  int32_t reserved;         /* 0 */
 } cd_params;
 
 /* Per-round record of the last run on a graph (cd_trace_get). */

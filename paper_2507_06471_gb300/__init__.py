@@ -39,7 +39,8 @@ class cd_params(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int32), ("max_levels", ctypes.c_int32),
                 ("threshold", ctypes.c_int64), ("tie_keep_current", ctypes.c_int32),
                 ("singleton_rule", ctypes.c_int32), ("use_frontier", ctypes.c_int32),
-                ("timing", ctypes.c_int32), ("sched_seed", ctypes.c_uint64)]
+                ("timing", ctypes.c_int32), ("sched_seed", ctypes.c_uint64),
+                ("aggregation", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class cd_round_trace(ctypes.Structure):

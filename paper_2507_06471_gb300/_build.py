@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcdgpu.so")
-SRCS = ["prims.cu", "graph.cu", "scan.cu", "aggregate.cu", "batch.cu", "noalloc.cu", "server.cu"]
+SRCS = ["prims.cu", "graph.cu", "scan.cu", "aggregate.cu", "batch.cu", "noalloc.cu", "server.cu", "hashagg.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "cdgpu.h")]
 FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]

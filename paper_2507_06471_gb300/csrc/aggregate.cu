@@ -199,7 +199,8 @@ int renumber(cd_graph* g, const int32_t* labels_dev, int32_t* newid_dev, int64_t
 }
 
 int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, int64_t k,
-              cd_graph** coarse_out) {
+              cd_graph** coarse_out, int mode) {
+  if (mode == 0 && g->n > 0 && k > 0) return aggregate_hash(g, labels_dev, newid_dev, k, coarse_out);
   cudaStream_t s = g->stream;
   const int64_t n = g->n, m = g->nnz;
   const int bits = ceil_log2_host(k);  // B < k fits in `bits` bits
@@ -421,7 +422,7 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
     levels = lvl + 1;
     if (k == cur->n) break;  // done: every vertex is its own community
     cd_graph* coarse = nullptr;
-    rc = aggregate(cur, cur->C, newid, k, &coarse);
+    rc = aggregate(cur, cur->C, newid, k, &coarse, p->aggregation);
     dev_free(newid, s);
     newid = nullptr;
     if (rc) break;

@@ -369,7 +369,7 @@ int cd_batch_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, i
     }
     // union of the graphs' coarse graphs, with the partition carried over
     cd_graph* coarse = nullptr;
-    if ((rc = aggregate(cur, cur->C, newid, k, &coarse))) break;
+    if ((rc = aggregate(cur, cur->C, newid, k, &coarse, p->aggregation))) break;
     if ((rc = dev_alloc_t(&gid_c, k, s))) break;
     if (cur->n > 0)
       CD_LAUNCH(k_batch_coarse_gid<<<grid_cap((cur->n + NT - 1) / NT), NT, 0, s>>>(cur->C, newid, cur->gid,

@@ -220,7 +220,10 @@ int begin_run(cd_graph* g, const cd_params* p);  // validates params, resets tra
 // aggregate.cu
 int renumber(cd_graph* g, const int32_t* labels_dev, int32_t* newid_dev, int64_t* k_out);
 int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, int64_t k,
-              cd_graph** coarse_out);
+              cd_graph** coarse_out, int mode = 0);
+// Aggregation by hash-combining per community (no sort of the arcs).
+int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, int64_t k,
+                   cd_graph** coarse_out);
 int modularity(cd_graph* g, const int32_t* labels_dev, double* q_out);
 
 // prims.cu: device-wide primitives on the graph's stream

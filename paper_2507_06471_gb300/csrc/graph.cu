@@ -638,6 +638,8 @@ int cd_params_default(cd_params* p) {
   p->use_frontier = 1;
   p->timing = 0;
   p->sched_seed = 0x5EED5EEDull;
+  p->aggregation = 0;
+  p->reserved = 0;
   return CD_OK;
 }
 

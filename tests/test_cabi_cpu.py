@@ -50,7 +50,7 @@ def test_status_strings_and_defaults_without_gpu():
 
 def test_struct_layouts_match_header():
     import paper_2507_06471_gb300 as cd
-    assert ctypes.sizeof(cd.cd_params) == 40
+    assert ctypes.sizeof(cd.cd_params) == 48
     assert ctypes.sizeof(cd.cd_round_trace) == 48
     assert ctypes.sizeof(cd.cd_kernel_profile) == 56
 
