@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
     ap.add_argument("--json-out", default=None)
+    ap.add_argument("--asynchronous", action="store_true",
+                    help="the asynchronous variant (moves take effect at once; not reproducible)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-requests", type=int, default=512,
                     help="served: how many requests of the 20,000-request stream to run")
@@ -640,7 +642,7 @@ def main():
     n, nnz = g.n, g.nnz
     labels_lpa = torch.empty(n, dtype=torch.int32, device="cuda")
     labels_lv = torch.empty(n, dtype=torch.int32, device="cuda")
-    params = cd.cd_params_default()
+    params = cd.cd_params_default(asynchronous=int(args.asynchronous))
     stream = torch.cuda.current_stream()
 
     # warm-up (untimed)
@@ -680,7 +682,7 @@ def main():
     w_h = None if g.w is None else g.w.cpu().pin_memory()
     lab_h1 = torch.empty(n, dtype=torch.int32).pin_memory()
     lab_h2 = torch.empty(n, dtype=torch.int32).pin_memory()
-    params_e2e = cd.cd_params_default()
+    params_e2e = cd.cd_params_default(asynchronous=int(args.asynchronous))
     e2e_value, e2e_s = None, 0.0
     if args.e2e_steps > 0:
         run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
@@ -720,7 +722,7 @@ def main():
                    "parallelism": f"replicas x{world}", "schedule": "synchronous rounds, SplitMix64 "
                    "deferral coin, strict-positive gain, smallest-id ties, singleton rule",
                    "max_iter": params.max_iter, "max_levels": params.max_levels,
-                   "threshold": params.threshold},
+                   "threshold": params.threshold, "asynchronous": bool(args.asynchronous)},
         "time_to_converge_ms": {"lpa_plus_louvain_step": ms_max / args.steps},
         "step": infos[-1],
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

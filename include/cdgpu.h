@@ -63,7 +63,11 @@ typedef struct cd_params {
   uint64_t sched_seed;      /* state of the deferral coin's SplitMix64 stream; default 0x5EED5EED */
   int32_t aggregation;      /* Louvain aggregation: 0 hash-combine per community (default), 1 radix sort
                                of all arcs; the coarse graphs have the same rows either way */
-  int32_t reserved;         /* 0 */
+  int32_t asynchronous;     /* 1: the asynchronous variant (Sec. III-A-2, Sec. III-B-1): a committed move
+                               takes effect at once and later decisions of the same round may see it
+                               (the deferral coin still applies: without it adjacent vertices swap
+                               labels in lockstep); results vary from run to run. 0 (default):
+                               synchronous rounds, reproducible */
 } cd_params;
 
 /* Per-round record of the last run on a graph (cd_trace_get). */

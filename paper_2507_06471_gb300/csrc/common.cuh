@@ -203,6 +203,7 @@ struct RunOpts {
   int tie_keep_current, singleton_rule, use_frontier;
   uint64_t sched_seed;
   int32_t level;
+  int async_mode = 0;  // committed moves take effect at once (the coin still defers half of them)
 };
 // Algorithm 1 / Algorithm 2 round loops on g->C (device). Louvain: g->C holds
 // the initial partition; sigma/csize are rebuilt from it.

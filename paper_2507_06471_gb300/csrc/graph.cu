@@ -639,7 +639,7 @@ int cd_params_default(cd_params* p) {
   p->timing = 0;
   p->sched_seed = 0x5EED5EEDull;
   p->aggregation = 0;
-  p->reserved = 0;
+  p->asynchronous = 0;
   return CD_OK;
 }
 

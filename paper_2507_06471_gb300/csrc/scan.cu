@@ -138,6 +138,11 @@ struct ScanCtx {
   const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
   const unsigned long long* small_cnt;
   int64_t n_items, nhubs, n_ev_items;
+  // asynchronous mode: a committed move is applied at once through these
+  int async_mode;
+  int32_t* C_w;
+  int64_t* sigma_w;  // null for LPA
+  int32_t* csize_w;
   // batched mode (gid == nullptr: one graph)
   const int32_t* gid;
   const int64_t* gbase;
@@ -196,6 +201,18 @@ __device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t c
   }
 }
 
+// Asynchronous mode: v's move from `cur` to `target` takes effect now.
+__device__ __forceinline__ void apply_now(const ScanCtx& s, int32_t v, int32_t cur, int32_t target) {
+  s.C_w[v] = target;
+  if (s.sigma_w) {
+    const int64_t d = s.degw[v];
+    atomicAdd((unsigned long long*)&s.sigma_w[cur], (unsigned long long)(-d));
+    atomicAdd((unsigned long long*)&s.sigma_w[target], (unsigned long long)d);
+    atomicSub(&s.csize_w[cur], 1);
+    atomicAdd(&s.csize_w[target], 1);
+  }
+}
+
 // One thread acts on a decision: append a committed move or count a deferral.
 // Returns 1 if the move was deferred.
 __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t cur, int32_t target) {
@@ -207,6 +224,7 @@ __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t c
     s.mv_v[pos] = v;
     s.mv_c[pos] = target;
     s.mv_a[pos] = cur;
+    if (s.async_mode) apply_now(s, v, cur, target);
     return 0;
   }
   return 1;
@@ -418,6 +436,7 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
         s.mv_v[pos] = v;
         s.mv_c[pos] = target;
         s.mv_a[pos] = cur;
+        if (s.async_mode) apply_now(s, v, cur, target);
       }
     }
     if (s.mark) {
@@ -1348,6 +1367,10 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.n_items = g->hub_items;
     s.nhubs = g->nhubs;
     s.n_ev_items = g->hub_eval_items;
+    s.async_mode = o.async_mode;
+    s.C_w = g->C;
+    s.sigma_w = louv ? g->sigma : nullptr;
+    s.csize_w = g->csize;
     s.gid = o.batched ? g->gid : nullptr;
     s.gbase = o.batched ? g->gbase : nullptr;
     s.gvol = o.batched ? g->gvol : nullptr;
@@ -1419,7 +1442,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       g->pending_bytes[mk.first] = bytes;
     }
     if (moves > 0) {
-      {
+      if (!o.async_mode) {  // asynchronous moves were applied when made
         KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
         const unsigned gt = grid_cap((moves + NT - 1) / NT);
         if (louv)
@@ -1537,6 +1560,7 @@ RunOpts opts_from(const cd_params* p, int32_t level) {
   o.use_frontier = p->use_frontier;
   o.sched_seed = p->sched_seed;
   o.level = level;
+  o.async_mode = p->asynchronous ? 1 : 0;
   return o;
 }
 
