@@ -719,7 +719,7 @@ def main():
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": wl_name, "description": WORKLOADS[args.workload], "n": n, "arcs": nnz,
                    "l2": "inputs larger than L2 (column array %.1f GB)" % (nnz * 4 / 1e9),
-                   "parallelism": f"replicas x{world}", "schedule": "synchronous rounds, SplitMix64 "
+                   "parallelism": f"replicas x{world}", "schedule": ("asynchronous rounds (moves applied at once), " if args.asynchronous else "synchronous rounds, ") + "SplitMix64 "
                    "deferral coin, strict-positive gain, smallest-id ties, singleton rule",
                    "max_iter": params.max_iter, "max_levels": params.max_levels,
                    "threshold": params.threshold, "asynchronous": bool(args.asynchronous)},

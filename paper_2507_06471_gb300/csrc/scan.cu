@@ -123,7 +123,7 @@ struct ScanCtx {
   int32_t* hub_hascur;
   int32_t* hub_done;
   int32_t* hub_mv;
-  int32_t* hub_rb;                   // per hub: 1 = rebuild from its row before its next evaluation
+  int32_t* hub_rb;                   // per hub: 1 = rebuild from its row, 2 = compact, before its next evaluation
   int32_t* hub_flist_w;              // hubs flagged this round (read back at the start of the next)
   unsigned long long* hub_fcnt_w;
   const int32_t* hub_flist_r;        // hubs flagged in the previous round
@@ -277,17 +277,27 @@ __device__ __forceinline__ int64_t group_sum(unsigned peers, int64_t wt, int64_t
 
 constexpr unsigned long long SLOT_EMPTY = ~0ull;
 
-// Flag hub h to be rebuilt from its row at the start of the next round; its
-// histogram is not updated until then. A hub is queued once, when first
-// flagged.
-__device__ __forceinline__ void hub_flag_rebuild(const ScanCtx& s, int32_t h) {
-  if (atomicExch(&s.hub_rb[h], 1) == 0) s.hub_flist_w[atomicAdd(s.hub_fcnt_w, 1ull)] = h;
+// Flag hub h for the start of the next round: HUB_REBUILD (an update was
+// lost; it is rebuilt from its row and not updated until then) or
+// HUB_COMPACT (it is consistent but too full; its live entries are rehashed).
+// A hub is queued once, when it is first flagged.
+constexpr int32_t HUB_REBUILD = 1, HUB_COMPACT = 2;
+
+__device__ __forceinline__ void hub_flag(const ScanCtx& s, int32_t h, int32_t how) {
+  const int32_t old = how == HUB_REBUILD ? atomicExch(&s.hub_rb[h], HUB_REBUILD) : atomicCAS(&s.hub_rb[h], 0, how);
+  if (old == 0) s.hub_flist_w[atomicAdd(s.hub_fcnt_w, 1ull)] = h;
 }
 
-// An update gives up after HUB_PROBE_MAX probes, and a hub whose claimed
-// slots pass 7/8 of its capacity is rebuilt: labels that leave keep their
-// slot (count 0), so a table fills up over the rounds and linear-probe chains
-// would otherwise grow without bound.
+// Slot of `label` in a table of `cap` slots (hub histograms, here and in the
+// shared-memory layouts built for them).
+__device__ __forceinline__ int64_t hub_home(int32_t label, int64_t cap) {
+  return (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
+}
+
+// An update gives up after HUB_PROBE_MAX probes (the hub is rebuilt), and a
+// hub whose claimed slots pass 7/8 of its capacity is compacted: labels that
+// leave keep their slot (count 0), so a table fills up over the rounds and
+// linear-probe chains would otherwise grow without bound.
 constexpr int HUB_PROBE_MAX = 64;
 
 // k_{h,label} += w in hub h's histogram (w may be negative: a neighbour left
@@ -298,11 +308,11 @@ constexpr int HUB_PROBE_MAX = 64;
 // or when a label to decrement is missing, and then flags the hub.
 template <bool BUILD>
 __device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
-  if (!BUILD && s.hub_rb[h]) return;
+  if (!BUILD && s.hub_rb[h] == HUB_REBUILD) return;
   const int64_t base = s.hub_tab[h];
   const int64_t cap = s.hub_tab[h + 1] - base;
   const int64_t lim = BUILD ? cap : (cap < HUB_PROBE_MAX ? cap : HUB_PROBE_MAX);
-  int64_t slot = (int64_t)(((uint64_t)((uint32_t)label * 2654435761u) * (uint64_t)cap) >> 32);
+  int64_t slot = hub_home(label, cap);
   bool claimed = false;
   if (!s.hub_wide) {
     unsigned long long* words = s.hub_slot + base;
@@ -345,9 +355,10 @@ __device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_
   }
   if (claimed) {
     const int32_t used = atomicAdd(&s.hub_used[h], 1) + 1;
-    if (BUILD || (int64_t)used * 8 <= cap * 7) return;
+    if (!BUILD && (int64_t)used * 8 > cap * 7) hub_flag(s, h, HUB_COMPACT);
+    return;
   }
-  hub_flag_rebuild(s, h);
+  hub_flag(s, h, HUB_REBUILD);
 }
 
 // Read slot i of a hub table at `base`: (label or -1 if empty, count).
@@ -713,25 +724,61 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
 // committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
 // therefore reads its distinct labels instead of its whole row.
 
+constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
+constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
+
 // Start of a round, a CTA per hub flagged in the previous round (every hub in
-// round 0): clear its table and queue its build items.
+// round 0). COMPACT (packed slots, table of at most HUB_PREP_SLOTS): the live
+// entries (count > 0) are rehashed into a fresh layout in shared memory, which
+// is written back with coalesced stores. REBUILD or a larger table: the table
+// is cleared (unless a single build item will overwrite it whole) and the
+// hub's build items are queued.
 __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* T = (unsigned long long*)smem;
   __shared__ unsigned long long pos;
+  __shared__ int n_live;
   const int64_t nf = (int64_t)*(volatile const unsigned long long*)s.hub_fcnt_r;
   for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
     const int32_t h = s.hub_flist_r[q];
     const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
-    for (int64_t i = threadIdx.x; i < cap; i += NT) {
-      if (!s.hub_wide) {
-        s.hub_slot[base + i] = SLOT_EMPTY;
-      } else {
-        s.hub_slot[2 * (base + i)] = SLOT_EMPTY;
-        s.hub_slot[2 * (base + i) + 1] = 0;
+    const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
+    if (s.hub_rb[h] == HUB_COMPACT && !s.hub_wide && cap <= HUB_PREP_SLOTS) {  // uniform in the CTA
+      for (int64_t i = threadIdx.x; i < cap; i += NT) T[i] = SLOT_EMPTY;
+      if (threadIdx.x == 0) n_live = 0;
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < cap; i += NT) {
+        const unsigned long long x = s.hub_slot[base + i];
+        if (x == SLOT_EMPTY || (x & 0xffffffffull) == 0) continue;
+        int64_t slot = hub_home((int32_t)(x >> 32), cap);
+        for (int64_t probe = 0; probe < cap; ++probe) {  // fewer live entries than slots: always ends
+          if (atomicCAS(&T[slot], SLOT_EMPTY, x) == SLOT_EMPTY) break;
+          slot = slot + 1 == cap ? 0 : slot + 1;
+        }
+        atomicAdd(&n_live, 1);
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < cap; i += NT) s.hub_slot[base + i] = T[i];
+      if (threadIdx.x == 0) {
+        s.hub_used[h] = n_live;
+        s.hub_rb[h] = 0;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (ni > 1 || s.hub_wide) {  // a single item lays the whole table out itself
+      for (int64_t i = threadIdx.x; i < cap; i += NT) {
+        if (!s.hub_wide) {
+          s.hub_slot[base + i] = SLOT_EMPTY;
+        } else {
+          s.hub_slot[2 * (base + i)] = SLOT_EMPTY;
+          s.hub_slot[2 * (base + i) + 1] = 0;
+        }
       }
     }
-    const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
     if (threadIdx.x == 0) {
       s.hub_used[h] = 0;
+      s.hub_rb[h] = HUB_REBUILD;  // cleared once built (start of the evaluate kernel)
       pos = atomicAdd(&s.hub_lcnt[0], (unsigned long long)ni);
     }
     __syncthreads();
@@ -771,13 +818,51 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
     group_insert<W, V, HUB_NT>(s, v, a0, end, threadIdx.x, keys, vals, occ, &occ_n, 13, stage);
     __syncthreads();
     const int nocc = occ_n;
-    for (int j = threadIdx.x; j < nocc; j += HUB_NT) {
-      const int slot = occ[j];
-      const int32_t c = keys[slot];
-      const int64_t k = (int64_t)vals[slot];
-      keys[slot] = EMPTY;
-      vals[slot] = 0;
-      hub_hist_add<true>(s, h, c, k);
+    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
+    if (s.hub_item_first[h + 1] - s.hub_item_first[h] == 1 && !s.hub_wide) {  // uniform in the CTA
+      // the whole histogram is here: lay the table out in shared memory (over
+      // the keys/values, at least 64 KB) and write it with coalesced stores
+      constexpr int PER = HUB_CHUNK / HUB_NT;  // distinct labels per thread at most
+      unsigned long long ent[PER];
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        const int j = threadIdx.x + r * HUB_NT;
+        ent[r] = SLOT_EMPTY;
+        if (j < nocc) {
+          const int slot = occ[j];
+          ent[r] = ((unsigned long long)(uint32_t)keys[slot] << 32) | (unsigned long long)(uint32_t)vals[slot];
+        }
+      }
+      __syncthreads();
+      unsigned long long* T = (unsigned long long*)smem;
+      for (int64_t i = threadIdx.x; i < cap; i += HUB_NT) T[i] = SLOT_EMPTY;
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < PER; ++r) {
+        if (ent[r] == SLOT_EMPTY) continue;
+        int64_t slot = hub_home((int32_t)(ent[r] >> 32), cap);
+        for (int64_t probe = 0; probe < cap; ++probe) {  // nocc <= deg < cap: always ends
+          if (atomicCAS(&T[slot], SLOT_EMPTY, ent[r]) == SLOT_EMPTY) break;
+          slot = slot + 1 == cap ? 0 : slot + 1;
+        }
+      }
+      __syncthreads();
+      for (int64_t i = threadIdx.x; i < cap; i += HUB_NT) s.hub_slot[base + i] = T[i];
+      if (threadIdx.x == 0) s.hub_used[h] = nocc;
+      __syncthreads();
+      for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {  // the tables for the next item
+        keys[j] = EMPTY;
+        vals[j] = 0;
+      }
+    } else {
+      for (int j = threadIdx.x; j < nocc; j += HUB_NT) {
+        const int slot = occ[j];
+        const int32_t c = keys[slot];
+        const int64_t k = (int64_t)vals[slot];
+        keys[slot] = EMPTY;
+        vals[slot] = 0;
+        hub_hist_add<true>(s, h, c, k);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) occ_n = 0;
@@ -1174,6 +1259,7 @@ int set_smem_attrs() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
   done = true;
@@ -1202,7 +1288,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_HUB) > 0) {
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
-      CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 8), NT, 0, st>>>(s));
+      CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
