@@ -25,7 +25,7 @@ constexpr int BLOCK_MAX = 1024;  // largest degree scanned through shared-memory
 // The runtime bin boundaries t_warp (warp vs 128-thread group) and t_hub
 // (group vs hub histogram) may be lowered below these capacities (autotuner).
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
-constexpr int HUB_SLICE = 4096;  // histogram slots per hub evaluate item
+constexpr int HUB_SLICE = 32768;  // histogram slots per hub evaluate item
 constexpr int HUB_SMALL = 8192;  // hubs of at most this many slots are evaluated by one warp
 constexpr int COL_PAD = 4;       // column arrays carry 4 spare entries for 16-byte loads
 

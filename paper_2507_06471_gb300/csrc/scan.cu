@@ -137,6 +137,7 @@ struct ScanCtx {
   const unsigned long long* ev_cnt;  // their number
   const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
   const unsigned long long* small_cnt;
+  int hub_upd;  // 0: neighbour moves do not update hub histograms (every hub is rebuilt next round)
   int64_t n_items, nhubs, n_ev_items;
   // asynchronous mode: a committed move is applied at once through these
   int async_mode;
@@ -299,6 +300,7 @@ __device__ __forceinline__ int64_t hub_home(int32_t label, int64_t cap) {
 // leave keep their slot (count 0), so a table fills up over the rounds and
 // linear-probe chains would otherwise grow without bound.
 constexpr int HUB_PROBE_MAX = 64;
+constexpr int64_t HUB_SKIP_DIV = 16;
 
 // k_{h,label} += w in hub h's histogram (w may be negative: a neighbour left
 // `label`; the count then stays >= 0). A packed slot is updated with one
@@ -379,7 +381,7 @@ __device__ __forceinline__ void hub_slot_read(const ScanCtx& s, int64_t base, in
 // w) changes u's histogram if u is a hub. The hub bitmap (n bits) stays in L2.
 __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u, int32_t A, int32_t c,
                                                     int64_t w) {
-  if (!((__ldg(&s.hub_bits[u >> 5]) >> (u & 31)) & 1u)) return;
+  if (!s.hub_upd || !((__ldg(&s.hub_bits[u >> 5]) >> (u & 31)) & 1u)) return;
   const int32_t h = s.hub_idx[u];
   hub_hist_add<false>(s, h, A, -w);
   hub_hist_add<false>(s, h, c, w);
@@ -1189,6 +1191,8 @@ __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = x;
 }
 
+__global__ void k_set_u64(unsigned long long* p, unsigned long long x) { *p = x; }
+
 __global__ void k_iota_i32(int32_t* a, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) a[i] = (int32_t)i;
@@ -1387,6 +1391,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
   if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fcur, 1, n, st));
   const int wbytes = g->wkind == W_UNIT ? 0 : g->wkind == W_I32 ? 4 : 8;
   int64_t total_moves = 0;
+  int64_t prev_moves = -1;
   int32_t rounds = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (g->timing)
@@ -1453,6 +1458,13 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.n_items = g->hub_items;
     s.nhubs = g->nhubs;
     s.n_ev_items = g->hub_eval_items;
+    // In a round that moves many vertices (the first of a run or level, or
+    // after one that moved more than 1/HUB_SKIP_DIV of them) the hub
+    // histograms are not updated move by move: every hub is rebuilt from its
+    // row at the start of the next round instead, which costs less than that
+    // many scattered updates.
+    const bool skip_upd = g->nhubs > 0 && (r == 0 || prev_moves * HUB_SKIP_DIV > n);
+    s.hub_upd = skip_upd ? 0 : 1;
     s.async_mode = o.async_mode;
     s.C_w = g->C;
     s.sigma_w = louv ? g->sigma : nullptr;
@@ -1545,6 +1557,13 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       }
       CD_CHECK(cudaGetLastError());
     }
+    if (skip_upd) {  // queue every hub for a rebuild at the start of the next round
+      CD_LAUNCH(k_fill_i32<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(g->hub_rb, g->nhubs, 1));
+      CD_LAUNCH(k_iota_i32<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(g->hub_flist + (r & 1) * g->nhubs,
+                                                                           g->nhubs));
+      CD_LAUNCH(k_set_u64<<<1, 1, 0, st>>>(g->hub_fcnt + (r & 1), (unsigned long long)g->nhubs));
+    }
+    prev_moves = moves;
     cd_round_trace tr;
     tr.level = o.level;
     tr.round = r;
