@@ -54,7 +54,9 @@ enum Ctr {
   C_MOVES = 0,   // append cursor of the move list = vertices moved this round
   C_DEFERRED,    // vertices whose move the coin deferred
   C_BIN0,        // then per bin: active, arcs, candidates
-  C_COUNT = C_BIN0 + 3 * NBINS
+  C_HUB_BARCS = C_BIN0 + 3 * NBINS,  // arcs read by hub table builds this round
+  C_HUB_BSLOTS,                      // table slots they (and the clears and compactions) wrote
+  C_COUNT
 };
 
 // Per-kernel profiling slots.

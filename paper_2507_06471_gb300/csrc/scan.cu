@@ -772,6 +772,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       if (threadIdx.x == 0) {
         s.hub_used[h] = n_live;
         s.hub_rb[h] = 0;
+        atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)(2 * cap));  // read and written
       }
       __syncthreads();
       continue;
@@ -787,6 +788,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       continue;
     }
     if (ni > 1 || s.hub_wide) {  // a single packed item lays the whole table out itself
+      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
       for (int64_t i = threadIdx.x; i < cap; i += NT) {
         if (!s.hub_wide) {
           s.hub_slot[base + i] = SLOT_EMPTY;
@@ -894,7 +896,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULL, claimed, o);
     if (lane == 0 && claimed) atomicAdd(&s.hub_used[h], claimed);
-    if (rank == 0 && threadIdx.x == 0) s.hub_rb[h] = 0;
+    if (rank == 0 && threadIdx.x == 0) {
+      s.hub_rb[h] = 0;
+      atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - beg));
+      atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
+    }
     cl.sync();  // the parts are written before they are cleared for the next hub
   }
 }
@@ -958,7 +964,10 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
       }
       __syncthreads();
       for (int64_t i = threadIdx.x; i < cap; i += HUB_NT) s.hub_slot[base + i] = T[i];
-      if (threadIdx.x == 0) s.hub_used[h] = nocc;
+      if (threadIdx.x == 0) {
+        s.hub_used[h] = nocc;
+        atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
+      }
       __syncthreads();
       for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {  // the tables for the next item
         keys[j] = EMPTY;
@@ -973,7 +982,9 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
         vals[slot] = 0;
         hub_hist_add<true>(s, h, c, k);
       }
+      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)nocc);
     }
+    if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - a0));
     __syncthreads();
     if (threadIdx.x == 0) occ_n = 0;
     __syncthreads();
@@ -1650,8 +1661,8 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       const int64_t ab = b >= 0 ? h[C_BIN0 + 3 * b] : 0;
       const int64_t rb = h[C_BIN0 + 3 * B_HUB + 1], cb = b >= 0 ? h[C_BIN0 + 3 * b + 2] : 0;
       double bytes;
-      if (b == -1)  // hub insert: arcs in, one table update per distinct label
-        bytes = (double)rb * (4 + 4 + wbytes) + (double)h[C_BIN0 + 3 * B_HUB + 2] * 12;
+      if (b == -1)  // hub table builds: the arcs they read, the slots they wrote
+        bytes = (double)h[C_HUB_BARCS] * (4 + 4 + wbytes) + (double)h[C_HUB_BSLOTS] * 8;
       else if (b == B_HUB)  // hub evaluate: the candidates of every active hub
         bytes = (double)cb * (12 + 12 + (louv ? 8 : 0)) + (double)ab * (8 + 4);
       else
