@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
 // committed move of a neighbour (k[old] -= w, k[new] += w). Evaluating a hub
 // therefore reads its distinct labels instead of its whole row.
 
-constexpr int HUB_CL_SLOTS = 24576;    // table slots per CTA of a cluster build (192 KB)
+constexpr int HUB_CL_SLOTS = 12288;    // table slots per CTA of a cluster build (96 KB: 2 CTAs per SM)
 constexpr size_t HUB_CL_SMEM = (size_t)HUB_CL_SLOTS * 8;
 constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
 constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
@@ -777,7 +777,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       __syncthreads();
       continue;
     }
-    if (!s.hub_wide && ni > 1 && cap <= 8 * HUB_CL_SLOTS) {  // a cluster builds it and writes the whole table
+    if (!s.hub_wide && cap <= 8 * HUB_CL_SLOTS) {  // a cluster builds it and writes the whole table
       if (threadIdx.x == 0) {
         const int c = cap <= HUB_CL_SLOTS ? 0 : cap <= 2 * HUB_CL_SLOTS ? 1 : cap <= 4 * HUB_CL_SLOTS ? 2 : 3;
         s.hub_used[h] = 0;
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       __syncthreads();
       continue;
     }
-    if (ni > 1 || s.hub_wide) {  // a single packed item lays the whole table out itself
+    {  // giant or two-word hubs: cleared here, built by items with global inserts
       if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
       for (int64_t i = threadIdx.x; i < cap; i += NT) {
         if (!s.hub_wide) {
@@ -907,8 +907,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
 constexpr int HUB_CAP = 2 * HUB_CHUNK;
 static_assert(HUB_CAP == 8192, "hub chunk table");
 
-// Rebuild of the queued hubs: every item is one HUB_CHUNK-arc chunk of a hub
-// row, combined in a shared-memory table, then added to the hub's histogram.
+// Rebuild of the queued hubs too large for a cluster (or with two-word
+// slots): every item is one HUB_CHUNK-arc chunk of a hub row, combined in a
+// shared-memory table, then added to the hub's histogram with global inserts.
 template <class W, class V>
 __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -934,57 +935,18 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
     group_insert<W, V, HUB_NT>(s, v, a0, end, threadIdx.x, keys, vals, occ, &occ_n, 13, stage);
     __syncthreads();
     const int nocc = occ_n;
-    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
-    if (s.hub_item_first[h + 1] - s.hub_item_first[h] == 1 && !s.hub_wide) {  // uniform in the CTA
-      // the whole histogram is here: lay the table out in shared memory (over
-      // the keys/values, at least 64 KB) and write it with coalesced stores
-      constexpr int PER = HUB_CHUNK / HUB_NT;  // distinct labels per thread at most
-      unsigned long long ent[PER];
-#pragma unroll
-      for (int r = 0; r < PER; ++r) {
-        const int j = threadIdx.x + r * HUB_NT;
-        ent[r] = SLOT_EMPTY;
-        if (j < nocc) {
-          const int slot = occ[j];
-          ent[r] = ((unsigned long long)(uint32_t)keys[slot] << 32) | (unsigned long long)(uint32_t)vals[slot];
-        }
-      }
-      __syncthreads();
-      unsigned long long* T = (unsigned long long*)smem;
-      for (int64_t i = threadIdx.x; i < cap; i += HUB_NT) T[i] = SLOT_EMPTY;
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < PER; ++r) {
-        if (ent[r] == SLOT_EMPTY) continue;
-        int64_t slot = hub_home((int32_t)(ent[r] >> 32), cap);
-        for (int64_t probe = 0; probe < cap; ++probe) {  // nocc <= deg < cap: always ends
-          if (atomicCAS(&T[slot], SLOT_EMPTY, ent[r]) == SLOT_EMPTY) break;
-          slot = slot + 1 == cap ? 0 : slot + 1;
-        }
-      }
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < cap; i += HUB_NT) s.hub_slot[base + i] = T[i];
-      if (threadIdx.x == 0) {
-        s.hub_used[h] = nocc;
-        atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
-      }
-      __syncthreads();
-      for (int j = threadIdx.x; j < HUB_CAP; j += HUB_NT) {  // the tables for the next item
-        keys[j] = EMPTY;
-        vals[j] = 0;
-      }
-    } else {
-      for (int j = threadIdx.x; j < nocc; j += HUB_NT) {
-        const int slot = occ[j];
-        const int32_t c = keys[slot];
-        const int64_t k = (int64_t)vals[slot];
-        keys[slot] = EMPTY;
-        vals[slot] = 0;
-        hub_hist_add<true>(s, h, c, k);
-      }
-      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)nocc);
+    for (int j = threadIdx.x; j < nocc; j += HUB_NT) {
+      const int slot = occ[j];
+      const int32_t c = keys[slot];
+      const int64_t k = (int64_t)vals[slot];
+      keys[slot] = EMPTY;
+      vals[slot] = 0;
+      hub_hist_add<true>(s, h, c, k);
     }
-    if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - a0));
+    if (threadIdx.x == 0) {
+      atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)nocc);
+      atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - a0));
+    }
     __syncthreads();
     if (threadIdx.x == 0) occ_n = 0;
     __syncthreads();
@@ -1416,10 +1378,10 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
-      CD_LAUNCH((k_hub_build_cl<W, 1><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 2><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 4><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 8><<<152, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 1><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 8><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
