@@ -237,13 +237,14 @@ int cd_server_destroy(cd_server* s);
 
 /* Degree bins (performance only; results never depend on them): vertices of
  * degree 33..t_warp are scanned by one warp, t_warp+1..t_hub by 128 threads
- * with a shared-memory table, and vertices above t_hub keep persistent label
- * histograms updated by their neighbours' moves. 32 <= t_warp <= 256,
- * t_warp <= t_hub <= 1024; defaults 256 and 1024. */
+ * (degree <= 1024) or 512 threads (<= 4096) with a shared-memory table, and
+ * vertices above t_hub keep persistent label histograms updated by their
+ * neighbours' moves. 32 <= t_warp <= 256, t_warp <= t_hub <= 4096; defaults
+ * 256 and 1024. */
 int cd_graph_set_bins(cd_graph* g, int32_t t_warp, int32_t t_hub);
 
 /* Autotuner: time `rounds` rounds of LPA plus `rounds` rounds of local moving
- * for every candidate (t_warp in {64,128,256}) x (t_hub in {256,512,1024}),
+ * for every candidate (t_warp in {64,128,256}) x (t_hub in {512,1024,2048,4096}),
  * keep the fastest bins on g (coarse Louvain levels inherit them) and report
  * them (outputs may be NULL). */
 int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp_out, int32_t* t_hub_out);

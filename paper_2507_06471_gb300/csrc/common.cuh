@@ -18,10 +18,11 @@ constexpr int32_t NOCAND = INT32_MAX;  // "no candidate" community id
 // Degree bins of the scan (degree = row length, loops included). Vertices
 // above BLOCK_MAX ("hubs") keep persistent label histograms instead of being
 // rescanned every round.
-enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_HUB, NBINS };
+enum Bin { B_T4 = 0, B_T8, B_T16, B_T32, B_WARP, B_BLK1, B_BLK4, B_HUB, NBINS };
 constexpr int WARP_MAX = 256;    // a warp per vertex, table <= 512 slots
 constexpr int BLK1_MAX = 1024;   // 128 threads per vertex, table <= 2048 slots
-constexpr int BLOCK_MAX = 1024;  // largest degree scanned through shared-memory tables
+constexpr int BLK4_MAX = 4096;   // a whole 512-thread CTA per vertex, table <= 8192 slots
+constexpr int BLOCK_MAX = 1024;  // default hub threshold (largest degree rescanned every round)
 // The runtime bin boundaries t_warp (warp vs 128-thread group) and t_hub
 // (group vs hub histogram) may be lowered below these capacities (autotuner).
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
@@ -63,7 +64,7 @@ enum Ctr {
 enum Kern {
   K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLK128,
   K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
-  K_HUB_MARK, K_FRONTIER, K_COUNT
+  K_HUB_MARK, K_FRONTIER, K_SCAN_BLK512, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -124,7 +125,7 @@ struct cd_graph {
   unsigned long long* hub_ccnt = nullptr;  // 4: their counts
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
-  int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads; above: hub
+  int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads (512 above 1024); above: hub
 
   // run state (allocated on first use)
   int32_t* C = nullptr;

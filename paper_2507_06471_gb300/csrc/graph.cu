@@ -19,7 +19,7 @@ namespace cd {
 const char* const kKernelNames[K_COUNT] = {
     "ingest",     "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
     "scan_blk128", "hub_build", "hub_eval",   "apply_moves", "renumber",    "agg_emit",
-    "radix_sort", "agg_reduce", "modularity", "hub_mark", "frontier"};
+    "radix_sort", "agg_reduce", "modularity", "hub_mark", "frontier", "scan_blk512"};
 
 static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};
@@ -114,8 +114,8 @@ __device__ __forceinline__ int bin_of(int64_t d, int t_warp = WARP_MAX, int t_hu
   if (d <= 16) return B_T16;
   if (d <= 32) return B_T32;
   if (d <= t_warp) return B_WARP;
-  if (d <= t_hub) return B_BLK1;
-  return B_HUB;
+  if (d > t_hub) return B_HUB;
+  return d <= BLK1_MAX ? B_BLK1 : B_BLK4;
 }
 
 __global__ void k_bin_count(const int64_t* __restrict__ off, int64_t n, int t_warp, int t_hub,
@@ -550,7 +550,7 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
 }  // namespace
 
 int rebin(cd_graph* g, int t_warp, int t_hub) {
-  if (t_warp < 32 || t_warp > WARP_MAX || t_hub < t_warp || t_hub > BLOCK_MAX) return CD_EINVAL;
+  if (t_warp < 32 || t_warp > WARP_MAX || t_hub < t_warp || t_hub > BLK4_MAX) return CD_EINVAL;
   if (t_warp == g->t_warp && t_hub == g->t_hub && g->bin_list) return CD_OK;
   CD_CHECK(cudaStreamSynchronize(g->stream));
   free_bins(g);

@@ -17,7 +17,8 @@
 // Degree bins (per graph, thresholds t_warp <= t_hub, defaults 256 and
 // 1024): degrees 1-4/5-8/9-16/17-32 use TILE lanes per vertex and group equal
 // labels with __match_any_sync; 33..t_warp a warp with a shared-memory
-// open-addressing table; up to t_hub 128 threads with a shared-memory table;
+// open-addressing table; up to t_hub 128 threads (degree <= 1024) or a whole
+// 512-thread CTA (<= 4096) with a shared-memory table;
 // larger degrees (hubs) keep persistent label histograms in global memory,
 // updated by their neighbours' moves, and many CTAs evaluate slices of a
 // hub's histogram with the last one deciding.
@@ -39,6 +40,7 @@ constexpr int NT = 256;  // threads of the tile and hub-evaluate kernels
 constexpr int NW = NT / 32;
 constexpr int WARP_CAP_SLOTS = 2 * WARP_MAX;   // table slots per warp-bin vertex
 constexpr int BLK1_CAP_SLOTS = 2 * BLK1_MAX;   // per 128-thread group
+constexpr int BLK4_CAP_SLOTS = 2 * BLK4_MAX;   // per 512-thread CTA
 constexpr bool BLK_PF = false;  // header prefetch in the 128-thread group kernel
 constexpr int BLK_WAVES = 1;    // grid of the 128-thread group kernel, in resident waves
 
@@ -1334,6 +1336,7 @@ template <class V> constexpr size_t group_smem(int gpb, int cap, int ntb) {
 }
 template <class V> constexpr size_t warp_smem() { return group_smem<V>(8, WARP_CAP_SLOTS, 256); }
 template <class V> constexpr size_t blk1_smem() { return group_smem<V>(4, BLK1_CAP_SLOTS, 512); }
+template <class V> constexpr size_t blk4_smem() { return group_smem<V>(1, BLK4_CAP_SLOTS, 512); }
 template <class V> constexpr size_t hub_smem() { return group_smem<V>(1, HUB_CAP, HUB_NT); }
 
 template <bool LOUV, class W, class V>
@@ -1342,6 +1345,8 @@ int set_smem_attrs() {
   if (done) return CD_OK;
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk4_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
@@ -1393,6 +1398,15 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) mark(B_HUB);
+  }
+  if (cnt(B_BLK4) > 0) {
+    {
+      KTimer t(g, K_SCAN_BLK512);
+      auto kern = k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false>;
+      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk4_smem<V>(), cnt(B_BLK4)), 512, blk4_smem<V>(), st>>>(
+          s, lst(B_BLK4), dcnt(B_BLK4))));
+    }
+    if (g->timing) mark(B_BLK4);
   }
   if (cnt(B_BLK1) > 0) {
     {
@@ -1819,7 +1833,7 @@ int cd_graph_set_bins(cd_graph* g, int32_t t_warp, int32_t t_hub) {
 int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp_out, int32_t* t_hub_out) {
   if (!g || !p || rounds < 1) return CD_EINVAL;
   static const int tw[] = {64, 128, 256};
-  static const int th[] = {256, 512, 1024};
+  static const int th[] = {512, 1024, 2048, 4096};
   int rc = ensure_run_state(g);
   if (rc) return rc;
   cudaEvent_t a, b;
@@ -1830,7 +1844,7 @@ int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp
   const bool timing = g->timing;
   g->timing = false;
   for (int i = 0; i < 3 && !rc; ++i)
-    for (int j = 0; j < 3 && !rc; ++j) {
+    for (int j = 0; j < 4 && !rc; ++j) {
       if (th[j] < tw[i]) continue;
       if ((rc = rebin(g, tw[i], th[j]))) break;
       RunOpts o = opts_from(p, 0);

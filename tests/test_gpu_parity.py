@@ -350,7 +350,7 @@ def test_wide_hub_histograms():
     assert abs(q - oq) <= 1e-12 * max(1.0, abs(oq))
 
 
-@pytest.mark.parametrize("bins", [(32, 32), (64, 256), (128, 512), (256, 1024)])
+@pytest.mark.parametrize("bins", [(32, 32), (64, 256), (128, 512), (256, 1024), (256, 2048), (64, 4096)])
 def test_bins_do_not_change_results(bins):
     # degree bins (and the hub threshold) only change how vertices are scanned
     g = graph("bins_w")
@@ -370,7 +370,7 @@ def test_autotune_keeps_results():
     off, cols, w = g.numpy()
     G = upload(g)
     tw, th = cd.cd_autotune(G.h, cd.cd_params_default(), 2)
-    assert tw in (64, 128, 256) and th in (256, 512, 1024) and th >= tw
+    assert tw in (64, 128, 256) and th in (512, 1024, 2048, 4096) and th >= tw
     lab, levels, q = G.louvain()
     olab, olv, oq, _ = oracle.louvain(off, cols, w)
     assert levels == olv and np.array_equal(lab.cpu().numpy(), olab)
