@@ -32,6 +32,7 @@ constexpr int AG_CHUNK = 4096;     // arcs per chunk of a larger segment
 constexpr int AG_WCAP = 2 * AG_WARP_MAX;
 constexpr int AG_CCAP = 2 * AG_CTA_MAX;
 constexpr int AG_SLICE = 1024;     // global-table slots per extraction item (tables are multiples)
+constexpr int AG_CNT = 512;        // threads of the CTA-per-segment kernel
 constexpr int32_t AG_EMPTY = -1;
 
 unsigned gcap(int64_t blocks, int64_t cap = 152 * 16) {
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_ag_warp(const int64_t* __restrict__ ssta
 // of a large segment (then the chunk's distinct count goes to dch and to the
 // segment's upper bound ub).
 template <bool CHUNK>
-__global__ void __launch_bounds__(NT) k_ag_cta(const int64_t* __restrict__ sstart, const int32_t* __restrict__ list,
+__global__ void __launch_bounds__(AG_CNT) k_ag_cta(const int64_t* __restrict__ sstart, const int32_t* __restrict__ list,
                                                const int64_t* __restrict__ ch_off, int64_t nitems, int32_t* ab,
                                                unsigned long long* aw, int64_t* __restrict__ ucnt,
                                                int32_t* __restrict__ dch, unsigned long long* __restrict__ ub) {
@@ -235,10 +236,10 @@ __global__ void __launch_bounds__(NT) k_ag_cta(const int64_t* __restrict__ sstar
   unsigned long long* vals = (unsigned long long*)smem;
   int32_t* keys = (int32_t*)(smem + (size_t)AG_CCAP * 8);
   unsigned long long* stage = (unsigned long long*)(smem + (size_t)AG_CCAP * 12) + (threadIdx.x >> 5) * 32;
-  uint16_t* occ = (uint16_t*)(smem + (size_t)AG_CCAP * 12 + (size_t)NW * 32 * 8);
+  uint16_t* occ = (uint16_t*)(smem + (size_t)AG_CCAP * 12 + (size_t)(AG_CNT / 32) * 32 * 8);
   __shared__ int occ_n;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < AG_CCAP; j += NT) {
+  for (int j = threadIdx.x; j < AG_CCAP; j += AG_CNT) {
     keys[j] = AG_EMPTY;
     vals[j] = 0;
   }
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(NT) k_ag_cta(const int64_t* __restrict__ sstar
     }
     const unsigned lg = lg_for(2 * len);
     // warps take interleaved 32-entry rows of the block
-    for (int64_t j = (int64_t)wid * 32; j < len; j += NT) {
+    for (int64_t j = (int64_t)wid * 32; j < len; j += AG_CNT) {
       const int64_t jj = j + lane;
       const bool ok = jj < len;
       const int32_t key = ok ? ab[p + jj] : (int32_t)(0x80000000u | (unsigned)lane);
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(NT) k_ag_cta(const int64_t* __restrict__ sstar
     }
     __syncthreads();  // every entry read and inserted before the block is overwritten
     const int nocc = occ_n;
-    for (int j = threadIdx.x; j < nocc; j += NT) {
+    for (int j = threadIdx.x; j < nocc; j += AG_CNT) {
       const int slot = occ[j];
       ab[p + j] = keys[slot];
       aw[p + j] = vals[slot];
@@ -489,15 +490,15 @@ int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_
       CD_CHECK(cudaMemsetAsync(ucnt, 0, k * sizeof(int64_t), s));  // large segments count by atomics
     }
     const size_t wsm = (size_t)NW * AG_WCAP * 12 + (size_t)NW * 32 * 8 + (size_t)NW * AG_WCAP * 2;
-    const size_t csm = (size_t)AG_CCAP * 12 + (size_t)NW * 32 * 8 + (size_t)AG_CCAP * 2;
+    const size_t csm = (size_t)AG_CCAP * 12 + (size_t)(AG_CNT / 32) * 32 * 8 + (size_t)AG_CCAP * 2;
     CD_CHECK(cudaFuncSetAttribute(k_ag_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
     CD_CHECK(cudaFuncSetAttribute(k_ag_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
     CD_CHECK(cudaFuncSetAttribute(k_ag_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
     if (nw > 0) CD_LAUNCH(k_ag_warp<<<gcap((nw + NW - 1) / NW, 152 * 4), NT, wsm, s>>>(sstart, wl, nw, ab, aw, ucnt));
     if (nc > 0)
-      CD_LAUNCH(k_ag_cta<false><<<gcap(nc, 152 * 2), NT, csm, s>>>(sstart, cl, nullptr, nc, ab, aw, ucnt, nullptr, nullptr));
+      CD_LAUNCH(k_ag_cta<false><<<gcap(nc, 152 * 2), AG_CNT, csm, s>>>(sstart, cl, nullptr, nc, ab, aw, ucnt, nullptr, nullptr));
     if (nl > 0) {
-      CD_LAUNCH(k_ag_cta<true><<<gcap(nch, 152 * 2), NT, csm, s>>>(sstart, ch_seg, ch_off, nch, ab, aw, ucnt, dch, ub));
+      CD_LAUNCH(k_ag_cta<true><<<gcap(nch, 152 * 2), AG_CNT, csm, s>>>(sstart, ch_seg, ch_off, nch, ab, aw, ucnt, dch, ub));
       CD_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
       CD_LAUNCH(k_ag_tables_size<<<gcap((nl + NT - 1) / NT), NT, 0, s>>>(ll, nl, ub, tlg, toff, cnt));
       unsigned long long slots = 0;

@@ -59,8 +59,8 @@ __device__ __forceinline__ bool commit_coin(uint64_t seed, int level, int round,
 
 // ------------------------------------------------------------------ keys
 
-template <bool LOUV> struct KeyOf { typedef int64_t T; };
-template <> struct KeyOf<true> { typedef i128 T; };
+template <bool LOUV, bool NK> struct KeyOf { typedef int64_t T; };
+template <> struct KeyOf<true, false> { typedef i128 T; };
 
 __device__ __forceinline__ int64_t shfl_xor_key(int64_t x, int o) {
   return __shfl_xor_sync(FULL, (long long)x, o);
@@ -174,28 +174,32 @@ __device__ __forceinline__ void count_change(const ScanCtx& s, int32_t v) {
   if (s.gcnt) atomicAdd(&s.gcnt[s.gid[v]], 1ull);
 }
 
-template <bool LOUV>
-__device__ __forceinline__ typename KeyOf<LOUV>::T cand_key(const ScanCtx& s, int32_t c, int64_t k,
+template <bool LOUV, bool NK>
+__device__ __forceinline__ typename KeyOf<LOUV, NK>::T cand_key(const ScanCtx& s, int32_t c, int64_t k,
                                                             int64_t d, int64_t vol) {
-  if constexpr (LOUV)
+  if constexpr (LOUV && NK)
+    return vol * k - d * s.sigma[c];  // each product < 2^62 when vol(V) < 2^31
+  else if constexpr (LOUV)
     return (i128)vol * k - (i128)d * s.sigma[c];
   else
     return k;
 }
 
 // The same key with Sigma_tot[c] already loaded.
-template <bool LOUV>
-__device__ __forceinline__ typename KeyOf<LOUV>::T cand_key_sg(int64_t sig, int64_t k, int64_t d, int64_t vol) {
-  if constexpr (LOUV)
+template <bool LOUV, bool NK>
+__device__ __forceinline__ typename KeyOf<LOUV, NK>::T cand_key_sg(int64_t sig, int64_t k, int64_t d, int64_t vol) {
+  if constexpr (LOUV && NK)
+    return vol * k - d * sig;
+  else if constexpr (LOUV)
     return (i128)vol * k - (i128)d * sig;
   else
     return k;
 }
 
 // Final decision of vertex v from the best candidate.
-template <bool LOUV>
+template <bool LOUV, bool NK>
 __device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t cur,
-                                          typename KeyOf<LOUV>::T bk, int32_t bc, bool has_cur,
+                                          typename KeyOf<LOUV, NK>::T bk, int32_t bc, bool has_cur,
                                           int64_t kcur, int64_t vol) {
   if (bc == NOCAND) return cur;
   if constexpr (!LOUV) {
@@ -203,7 +207,7 @@ __device__ __forceinline__ int32_t decide(const ScanCtx& s, int32_t v, int32_t c
     return bc;
   } else {
     int64_t d = s.degw[v];
-    i128 G = bk - (i128)vol * kcur + (i128)d * (s.sigma[cur] - d);
+    i128 G = (i128)bk - (i128)vol * kcur + (i128)d * (s.sigma[cur] - d);
     if (G <= 0) return cur;  // only strictly positive gains
     if (s.singleton_rule && s.csize[cur] == 1 && s.csize[bc] == 1 && bc > cur) return cur;
     return bc;
@@ -398,10 +402,10 @@ __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u,
 // ------------------------------------------------------------------ tiles
 
 // TILE lanes per vertex, one arc per lane (degree <= TILE).
-template <int TILE, bool LOUV, class W>
+template <int TILE, bool LOUV, class W, bool NK>
 __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* __restrict__ list,
                                                   const unsigned long long* __restrict__ count_p, int bin) {
-  typedef typename KeyOf<LOUV>::T K;
+  typedef typename KeyOf<LOUV, NK>::T K;
   const int64_t count = (int64_t)*count_p;
   __shared__ int64_t stage[NW][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -438,11 +442,11 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
     const int64_t dv = (LOUV && act) ? s.degw[v] : 0;
     const int64_t volv = (LOUV && act) ? vol_of(s, v) : 0;
     const bool ok = leader && (!LOUV || lbl != cur);
-    K bk = ok ? cand_key<LOUV>(s, lbl, gsum, dv, volv) : K(0);
+    K bk = ok ? cand_key<LOUV, NK>(s, lbl, gsum, dv, volv) : K(0);
     int32_t bc = ok ? lbl : NOCAND;
     reduce_best(bk, bc, TILE);
     int32_t target = cur;
-    if (act) target = decide<LOUV>(s, v, cur, bk, bc, cm != 0, kcur, volv);
+    if (act) target = decide<LOUV, NK>(s, v, cur, bk, bc, cm != 0, kcur, volv);
     const bool want = act && target != cur;
     const bool commit = want && commit_coin(s.seed, s.level, s.round, local_id(s, v));
     if (want && sub == 0) count_change(s, v);
@@ -554,10 +558,10 @@ __device__ __forceinline__ void group_insert(const ScanCtx& s, int32_t v, int64_
 
 // Read a group's table through its occupied list: every listed slot is a
 // candidate; the slot is cleared for the next vertex.
-template <bool LOUV, class V, int GROUP>
+template <bool LOUV, class V, int GROUP, bool NK>
 __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_t dv, int64_t vol,
                                            int gl, int32_t* keys, V* vals, const uint16_t* occ, int nocc,
-                                           typename KeyOf<LOUV>::T& bk, int32_t& bc, bool& hc,
+                                           typename KeyOf<LOUV, NK>::T& bk, int32_t& bc, bool& hc,
                                            int64_t& kc, int64_t& ncand) {
   constexpr int EB = 2;  // candidates per thread per batch: the Sigma_tot gathers go out together
   for (int j0 = gl; j0 < nocc; j0 += EB * GROUP) {
@@ -587,7 +591,7 @@ __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_
         kc = k[q];
         if (LOUV) continue;
       }
-      const typename KeyOf<LOUV>::T key = cand_key_sg<LOUV>(sg[q], k[q], dv, vol);
+      const typename KeyOf<LOUV, NK>::T key = cand_key_sg<LOUV, NK>(sg[q], k[q], dv, vol);
       if (better(key, c[q], bk, bc)) {
         bk = key;
         bc = c[q];
@@ -617,10 +621,10 @@ __device__ __forceinline__ VHdr load_hdr(const ScanCtx& s, int32_t v, bool valid
 
 // GROUP threads per vertex (a warp, or a named-barrier group of 128 or 512
 // threads), each group with its own CAP-slot shared-memory table.
-template <bool LOUV, class W, class V, int GROUP, int NTB, int CAP, int BIN, bool PF>
+template <bool LOUV, class W, class V, int GROUP, int NTB, int CAP, int BIN, bool PF, bool NK>
 __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5) : 2)
     k_scan_group(ScanCtx s, const int32_t* __restrict__ list, const unsigned long long* __restrict__ count_p) {
-  typedef typename KeyOf<LOUV>::T K;
+  typedef typename KeyOf<LOUV, NK>::T K;
   const int64_t count = (int64_t)*count_p;
   constexpr int GPB = NTB / GROUP;  // groups per CTA
   constexpr int WPG = GROUP / 32;   // warps per group
@@ -684,7 +688,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
     int32_t bc = NOCAND;
     bool hc = false;
     int64_t kc = 0;
-    group_eval<LOUV, V, GROUP>(s, cur, dv, volv, gl, keys, vals, occ, nocc, bk, bc, hc, kc, n_cand);
+    group_eval<LOUV, V, GROUP, NK>(s, cur, dv, volv, gl, keys, vals, occ, nocc, bk, bc, hc, kc, n_cand);
     reduce_best(bk, bc, 32);
     unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
@@ -705,7 +709,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
       }
     }
     if (gl == 0) {
-      const int32_t target = decide<LOUV>(s, v, cur, bk, bc, hm != 0, kc, volv);
+      const int32_t target = decide<LOUV, NK>(s, v, cur, bk, bc, hm != 0, kc, volv);
       const int def = act_single(s, v, cur, target);
       n_def += def;
       ++n_act;
@@ -958,11 +962,11 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
 // Decision of hub h (one thread): act on it, and queue the mark items of a
 // committed move (the neighbours are flagged and their hub histograms
 // updated by k_hub_mark).
-template <bool LOUV>
+template <bool LOUV, bool NK>
 __device__ __forceinline__ void hub_decide(const ScanCtx& s, int32_t h, int32_t v, int32_t cur,
-                                           typename KeyOf<LOUV>::T fk, int32_t fc, bool hc, int64_t kc,
+                                           typename KeyOf<LOUV, NK>::T fk, int32_t fc, bool hc, int64_t kc,
                                            int64_t volv, int64_t& n_act, int64_t& n_arcs, int64_t& n_def) {
-  const int32_t target = decide<LOUV>(s, v, cur, fk, fc, hc, kc, volv);
+  const int32_t target = decide<LOUV, NK>(s, v, cur, fk, fc, hc, kc, volv);
   const int def = act_single(s, v, cur, target);
   n_def += def;
   if (target != cur && !def) {
@@ -979,9 +983,9 @@ __device__ __forceinline__ void hub_decide(const ScanCtx& s, int32_t h, int32_t 
 
 // A small hub (at most HUB_SMALL slots) is evaluated by one warp: no partial
 // results, no cross-CTA combination.
-template <bool LOUV>
+template <bool LOUV, bool NK>
 __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
-  typedef typename KeyOf<LOUV>::T K;
+  typedef typename KeyOf<LOUV, NK>::T K;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
@@ -1022,7 +1026,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
           kc = k[j];
           if (LOUV) continue;
         }
-        const K key = cand_key_sg<LOUV>(sg[j], k[j], dv, volv);
+        const K key = cand_key_sg<LOUV, NK>(sg[j], k[j], dv, volv);
         if (better(key, c[j], bk, bc)) {
           bk = key;
           bc = c[j];
@@ -1032,7 +1036,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
     reduce_best(bk, bc, 32);
     const unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
-    if (lane == 0) hub_decide<LOUV>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def);
+    if (lane == 0) hub_decide<LOUV, NK>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def);
   }
   flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
 }
@@ -1040,9 +1044,9 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
 // Every item scans HUB_SLICE histogram entries of one active hub; the last
 // item of a hub to finish combines the partial bests and decides. Entries
 // with weight 0 (labels that left the neighbourhood) are not candidates.
-template <bool LOUV>
+template <bool LOUV, bool NK>
 __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
-  typedef typename KeyOf<LOUV>::T K;
+  typedef typename KeyOf<LOUV, NK>::T K;
   __shared__ K red_k[NW];
   __shared__ int32_t red_c[NW];
   __shared__ int s_last;
@@ -1093,7 +1097,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
           s.hub_hascur[h] = 1;
           if (LOUV) continue;
         }
-        const K key = cand_key_sg<LOUV>(sg[j], k[j], dv, volv);
+        const K key = cand_key_sg<LOUV, NK>(sg[j], k[j], dv, volv);
         if (better(key, c[j], bk, bc)) {
           bk = key;
           bc = c[j];
@@ -1136,7 +1140,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       }
       const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
       const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
-      hub_decide<LOUV>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def);
+      hub_decide<LOUV, NK>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def);
       s.hub_done[h] = 0;
       s.hub_cur[h] = 0;
       s.hub_hascur[h] = 0;
@@ -1339,15 +1343,15 @@ template <class V> constexpr size_t blk1_smem() { return group_smem<V>(4, BLK1_C
 template <class V> constexpr size_t blk4_smem() { return group_smem<V>(1, BLK4_CAP_SLOTS, 512); }
 template <class V> constexpr size_t hub_smem() { return group_smem<V>(1, HUB_CAP, HUB_NT); }
 
-template <bool LOUV, class W, class V>
+template <bool LOUV, class W, class V, bool NK>
 int set_smem_attrs() {
   static std::atomic<bool> done{false};  // idempotent; threads may race here
   if (done) return CD_OK;
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk4_smem<V>()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
@@ -1369,10 +1373,10 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
   return b;
 }
 
-template <bool LOUV, class W, class V>
+template <bool LOUV, class W, class V, bool NK>
 int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned long long* counts,
                  std::vector<std::pair<size_t, int>>& marks) {
-  int rc = set_smem_attrs<LOUV, W, V>();
+  int rc = set_smem_attrs<LOUV, W, V, NK>();
   if (rc) return rc;
   cudaStream_t st = g->stream;
   auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
@@ -1393,16 +1397,16 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_EVAL);
       if (g->n_small_hubs > 0)
-        CD_LAUNCH(k_hub_eval_small<LOUV><<<wave_grid(k_hub_eval_small<LOUV>, NT, 0, (g->n_small_hubs + NW - 1) / NW),
+        CD_LAUNCH(k_hub_eval_small<LOUV, NK><<<wave_grid(k_hub_eval_small<LOUV, NK>, NT, 0, (g->n_small_hubs + NW - 1) / NW),
                                            NT, 0, st>>>(s));
-      CD_LAUNCH(k_hub_eval<LOUV><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
+      CD_LAUNCH(k_hub_eval<LOUV, NK><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
     }
     if (g->timing) mark(B_HUB);
   }
   if (cnt(B_BLK4) > 0) {
     {
       KTimer t(g, K_SCAN_BLK512);
-      auto kern = k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false>;
+      auto kern = k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false, NK>;
       CD_LAUNCH((kern<<<wave_grid(kern, 512, blk4_smem<V>(), cnt(B_BLK4)), 512, blk4_smem<V>(), st>>>(
           s, lst(B_BLK4), dcnt(B_BLK4))));
     }
@@ -1411,7 +1415,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_BLK1) > 0) {
     {
       KTimer t(g, K_SCAN_BLK128);
-      auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF>;
+      auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF, NK>;
       CD_LAUNCH((kern<<<grid_cap((cnt(B_BLK1) + 3) / 4, BLK_WAVES * resident_ctas((const void*)kern, 512,
                                                                                 blk1_smem<V>())),
                         512, blk1_smem<V>(), st>>>(
@@ -1422,7 +1426,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP);
-      auto kern = k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true>;
+      auto kern = k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true, NK>;
       CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + NW - 1) / NW), 256, warp_smem<V>(),
                         st>>>(s, lst(B_WARP), dcnt(B_WARP))));
     }
@@ -1431,7 +1435,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_T32) > 0) {
     {
       KTimer t(g, K_SCAN_T32);
-      auto kern = k_scan_tile<32, LOUV, W>;
+      auto kern = k_scan_tile<32, LOUV, W, NK>;
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T32) + NW - 1) / (NW)), NT, 0, st>>>(
           s, lst(B_T32), dcnt(B_T32), B_T32));
     }
@@ -1440,7 +1444,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_T16) > 0) {
     {
       KTimer t(g, K_SCAN_T16);
-      auto kern = k_scan_tile<16, LOUV, W>;
+      auto kern = k_scan_tile<16, LOUV, W, NK>;
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
           s, lst(B_T16), dcnt(B_T16), B_T16));
     }
@@ -1449,7 +1453,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_T8) > 0) {
     {
       KTimer t(g, K_SCAN_T8);
-      auto kern = k_scan_tile<8, LOUV, W>;
+      auto kern = k_scan_tile<8, LOUV, W, NK>;
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
           s, lst(B_T8), dcnt(B_T8), B_T8));
     }
@@ -1458,7 +1462,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_T4) > 0) {
     {
       KTimer t(g, K_SCAN_T4);
-      auto kern = k_scan_tile<4, LOUV, W>;
+      auto kern = k_scan_tile<4, LOUV, W, NK>;
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
           s, lst(B_T4), dcnt(B_T4), B_T4));
     }
@@ -1466,6 +1470,19 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   }
   CD_CHECK(cudaGetLastError());
   return CD_OK;
+}
+
+template <bool LOUV, bool NK>
+int dispatch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned long long* counts,
+                   std::vector<std::pair<size_t, int>>& marks, bool v32) {
+  if (g->wkind == W_UNIT)
+    return v32 ? launch_round<LOUV, WUnit, uint32_t, NK>(g, s, lists, counts, marks)
+               : launch_round<LOUV, WUnit, unsigned long long, NK>(g, s, lists, counts, marks);
+  if (g->wkind == W_I32)
+    return v32 ? launch_round<LOUV, WI32, uint32_t, NK>(g, s, lists, counts, marks)
+               : launch_round<LOUV, WI32, unsigned long long, NK>(g, s, lists, counts, marks);
+  return v32 ? launch_round<LOUV, WI64, uint32_t, NK>(g, s, lists, counts, marks)
+             : launch_round<LOUV, WI64, unsigned long long, NK>(g, s, lists, counts, marks);
 }
 
 int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out,
@@ -1605,19 +1622,12 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
     if (louv) {
-      if (g->wkind == W_UNIT) rc = v32 ? launch_round<true, WUnit, uint32_t>(g, s, lists, counts, marks)
-                                       : launch_round<true, WUnit, unsigned long long>(g, s, lists, counts, marks);
-      else if (g->wkind == W_I32) rc = v32 ? launch_round<true, WI32, uint32_t>(g, s, lists, counts, marks)
-                                           : launch_round<true, WI32, unsigned long long>(g, s, lists, counts, marks);
-      else rc = v32 ? launch_round<true, WI64, uint32_t>(g, s, lists, counts, marks)
-                    : launch_round<true, WI64, unsigned long long>(g, s, lists, counts, marks);
+      // Louvain candidate keys vol(V) k - deg_w(v) Sigma_tot need 128 bits in
+      // general; when vol(V) < 2^31 each product is < 2^62 and they fit in 64
+      if (g->vol < ((int64_t)1 << 31)) rc = dispatch_round<true, true>(g, s, lists, counts, marks, v32);
+      else rc = dispatch_round<true, false>(g, s, lists, counts, marks, v32);
     } else {
-      if (g->wkind == W_UNIT) rc = v32 ? launch_round<false, WUnit, uint32_t>(g, s, lists, counts, marks)
-                                       : launch_round<false, WUnit, unsigned long long>(g, s, lists, counts, marks);
-      else if (g->wkind == W_I32) rc = v32 ? launch_round<false, WI32, uint32_t>(g, s, lists, counts, marks)
-                                           : launch_round<false, WI32, unsigned long long>(g, s, lists, counts, marks);
-      else rc = v32 ? launch_round<false, WI64, uint32_t>(g, s, lists, counts, marks)
-                    : launch_round<false, WI64, unsigned long long>(g, s, lists, counts, marks);
+      rc = dispatch_round<false, false>(g, s, lists, counts, marks, v32);
     }
     if (rc) break;
     if (g->timing) cudaEventRecord(ev[1], st);

@@ -409,3 +409,34 @@ def test_aggregate_segment_classes():
         np.testing.assert_array_equal(gc, oc)
         np.testing.assert_array_equal(gwt, owt)
         C.close()
+
+
+@pytest.mark.parametrize("target", [2**31 - 4096, 2**31 + 4096])
+def test_key_width_boundary(target):
+    # Louvain keys are 64-bit when vol(V) < 2^31 and 128-bit otherwise; a graph
+    # on either side of the boundary must give the oracle's result
+    rng = np.random.default_rng(21)
+    base = synth.sbm(3000, 30, "0.05", "0.002", seed=22)
+    bu = np.repeat(np.arange(base.n), np.diff(base.off.numpy()))
+    bv = base.cols.numpy().astype(np.int64)
+    keep = bu < bv
+    edges = list(zip(bu[keep].tolist(), bv[keep].tolist()))
+    m = len(edges)
+    half = target // 2  # vol = 2 * sum of edge weights
+    ws = np.full(m, half // m, dtype=np.int64)
+    ws[:half % m] += 1
+    idx = rng.permutation(m)
+    a, b = idx[: m // 2], idx[m // 2: 2 * (m // 2)]
+    delta = rng.integers(0, ws[a] - 1)
+    ws[a] -= delta
+    ws[b] += delta
+    assert ws.min() >= 1 and int(ws.sum()) == half
+    g = synth.from_edge_list(base.n, edges, ws.tolist())
+    off, cols, w = g.numpy()
+    vol = oracle.degw(off, cols, w)[1]
+    assert (vol < 2**31) == (target < 2**31)
+    G = upload(g)
+    lab, levels, q = G.louvain()
+    olab, olv, oq, _ = oracle.louvain(off, cols, w)
+    assert levels == olv and np.array_equal(lab.cpu().numpy(), olab)
+    assert abs(q - oq) <= 1e-12 * max(1.0, abs(oq))
