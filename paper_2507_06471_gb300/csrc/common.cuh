@@ -130,6 +130,7 @@ struct cd_graph {
   // run state (allocated on first use)
   int32_t* C = nullptr;
   int64_t* sigma = nullptr;
+  uint32_t* sigma32 = nullptr;  // 32-bit copy for the gathers (allocated on first use)
   int32_t* csize = nullptr;
   uint8_t* flag[2] = {nullptr, nullptr};
   int32_t* mv_v = nullptr;  // committed moves: vertex, new label, old label

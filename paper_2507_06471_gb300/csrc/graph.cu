@@ -313,6 +313,7 @@ void free_arrays(cd_graph* g) {
                 g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
                 g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
                 g->hub_blist,    g->hub_mlist,     g->hub_lcnt,     g->C,            g->sigma,        g->csize,
+                g->sigma32,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
                 g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
                 g->gfrozen,      g->gcnt};

@@ -100,6 +100,7 @@ struct ScanCtx {
   int64_t vol;
   const int32_t* C;
   const int64_t* sigma;
+  const uint32_t* sigma32;  // 32-bit copy of sigma for the gathers (vol(V) < 2^31, synchronous), or null
   const int32_t* csize;
   const uint8_t* flag_cur;
   uint8_t* flag_nxt;
@@ -174,11 +175,21 @@ __device__ __forceinline__ void count_change(const ScanCtx& s, int32_t v) {
   if (s.gcnt) atomicAdd(&s.gcnt[s.gid[v]], 1ull);
 }
 
+// Sigma_tot[c] for a candidate: from the 32-bit copy when there is one
+// (half the bytes of the random gather).
+template <bool NK>
+__device__ __forceinline__ int64_t sig_of(const ScanCtx& s, int32_t c) {
+  if constexpr (NK) {
+    if (s.sigma32) return (int64_t)s.sigma32[c];
+  }
+  return s.sigma[c];
+}
+
 template <bool LOUV, bool NK>
 __device__ __forceinline__ typename KeyOf<LOUV, NK>::T cand_key(const ScanCtx& s, int32_t c, int64_t k,
                                                             int64_t d, int64_t vol) {
   if constexpr (LOUV && NK)
-    return vol * k - d * s.sigma[c];  // each product < 2^62 when vol(V) < 2^31
+    return vol * k - d * sig_of<NK>(s, c);  // each product < 2^62 when vol(V) < 2^31
   else if constexpr (LOUV)
     return (i128)vol * k - (i128)d * s.sigma[c];
   else
@@ -581,7 +592,7 @@ __device__ __forceinline__ void group_eval(const ScanCtx& s, int32_t cur, int64_
       }
     }
 #pragma unroll
-    for (int q = 0; q < EB; ++q) sg[q] = (LOUV && c[q] >= 0) ? s.sigma[c[q]] : 0;
+    for (int q = 0; q < EB; ++q) sg[q] = (LOUV && c[q] >= 0) ? sig_of<NK>(s, c[q]) : 0;
 #pragma unroll
     for (int q = 0; q < EB; ++q) {
       if (c[q] < 0) continue;
@@ -1016,7 +1027,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
         if (x < cap) hub_slot_read(s, base, x, c[j], k[j]);
       }
 #pragma unroll
-      for (int j = 0; j < U; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? s.sigma[c[j]] : 0;
+      for (int j = 0; j < U; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? sig_of<NK>(s, c[j]) : 0;
 #pragma unroll
       for (int j = 0; j < U; ++j) {
         if (c[j] < 0 || k[j] == 0) continue;
@@ -1087,7 +1098,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
         if (x < e1) hub_slot_read(s, base, x, c[j], k[j]);
       }
 #pragma unroll
-      for (int j = 0; j < HB; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? s.sigma[c[j]] : 0;
+      for (int j = 0; j < HB; ++j) sg[j] = (LOUV && c[j] >= 0 && k[j] != 0) ? sig_of<NK>(s, c[j]) : 0;
 #pragma unroll
       for (int j = 0; j < HB; ++j) {
         if (c[j] < 0 || k[j] == 0) continue;  // unused entry, or a label that left
@@ -1279,6 +1290,23 @@ __global__ void k_fill_i32(int32_t* a, int64_t n, int32_t x) {
 }
 
 __global__ void k_set_u64(unsigned long long* p, unsigned long long x) { *p = x; }
+
+__global__ void k_sigma32_all(const int64_t* __restrict__ sigma, int64_t n, uint32_t* __restrict__ s32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) s32[i] = (uint32_t)sigma[i];
+}
+
+// After the moves of a round are applied: refresh the copies of the
+// communities they touched (plain stores of the final values).
+__global__ void k_sigma32_moves(const int32_t* __restrict__ mv_a, const int32_t* __restrict__ mv_c, int64_t nmoves,
+                                const int64_t* __restrict__ sigma, uint32_t* __restrict__ s32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < nmoves; m += stride) {
+    const int32_t a = mv_a[m], c = mv_c[m];
+    s32[a] = (uint32_t)sigma[a];
+    s32[c] = (uint32_t)sigma[c];
+  }
+}
 
 __global__ void k_iota_i32(int32_t* a, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1512,6 +1540,15 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
   const int wbytes = g->wkind == W_UNIT ? 0 : g->wkind == W_I32 ? 4 : 8;
   int64_t total_moves = 0;
   int64_t prev_moves = -1;
+  // 32-bit Sigma_tot copy for the gathers (synchronous Louvain, vol(V) < 2^31)
+  const bool use_s32 = louv && !o.async_mode && g->vol < ((int64_t)1 << 31) && n > 0;
+  if (use_s32) {
+    if (!g->sigma32) {
+      int rc2 = dev_alloc_t(&g->sigma32, n, st);
+      if (rc2) return rc2;
+    }
+    CD_LAUNCH(k_sigma32_all<<<grid_cap((n + NT - 1) / NT), NT, 0, st>>>(g->sigma, n, g->sigma32));
+  }
   int32_t rounds = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (g->timing)
@@ -1535,6 +1572,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.vol = g->vol;
     s.C = g->C;
     s.sigma = g->sigma;
+    s.sigma32 = use_s32 ? g->sigma32 : nullptr;
     s.csize = g->csize;
     s.flag_cur = fcur;
     s.flag_nxt = fnxt;
@@ -1659,8 +1697,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       if (!o.async_mode) {  // asynchronous moves were applied when made
         KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
         const unsigned gt = grid_cap((moves + NT - 1) / NT);
-        if (louv)
+        if (louv) {
           CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+          if (use_s32)
+            CD_LAUNCH(k_sigma32_moves<<<gt, NT, 0, st>>>(g->mv_a, g->mv_c, moves, g->sigma, g->sigma32));
+        }
         else
           CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
       }
