@@ -41,8 +41,6 @@ constexpr int NW = NT / 32;
 constexpr int WARP_CAP_SLOTS = 2 * WARP_MAX;   // table slots per warp-bin vertex
 constexpr int BLK1_CAP_SLOTS = 2 * BLK1_MAX;   // per 128-thread group
 constexpr int BLK4_CAP_SLOTS = 2 * BLK4_MAX;   // per 512-thread CTA
-constexpr bool BLK_PF = false;  // header prefetch in the 128-thread group kernel
-constexpr int BLK_WAVES = 1;    // grid of the 128-thread group kernel, in resident waves
 
 // ------------------------------------------------------------------ coin
 
@@ -1379,7 +1377,7 @@ int set_smem_attrs() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk4_smem<V>()));
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF, NK>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
@@ -1443,10 +1441,8 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_BLK1) > 0) {
     {
       KTimer t(g, K_SCAN_BLK128);
-      auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, BLK_PF, NK>;
-      CD_LAUNCH((kern<<<grid_cap((cnt(B_BLK1) + 3) / 4, BLK_WAVES * resident_ctas((const void*)kern, 512,
-                                                                                blk1_smem<V>())),
-                        512, blk1_smem<V>(), st>>>(
+      auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, false, NK>;
+      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk1_smem<V>(), (cnt(B_BLK1) + 3) / 4), 512, blk1_smem<V>(), st>>>(
           s, lst(B_BLK1), dcnt(B_BLK1))));
     }
     if (g->timing) mark(B_BLK1);
