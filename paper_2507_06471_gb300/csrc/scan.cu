@@ -748,7 +748,9 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
 // therefore reads its distinct labels instead of its whole row.
 
 constexpr int HUB_CL_SLOTS = 12288;    // table slots per CTA of a cluster build (96 KB: 2 CTAs per SM)
-constexpr size_t HUB_CL_SMEM = (size_t)HUB_CL_SLOTS * 8;
+constexpr int HUB_CL1_SLOTS = 8192;    // a one-CTA build (64 KB: 3 CTAs per SM)
+__host__ __device__ constexpr int hub_cl_slots(int c) { return c == 1 ? HUB_CL1_SLOTS : HUB_CL_SLOTS; }
+__host__ __device__ constexpr size_t hub_cl_smem(int c) { return (size_t)hub_cl_slots(c) * 8; }
 constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
 constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
 
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
     }
     if (!s.hub_wide && cap <= 8 * HUB_CL_SLOTS) {  // a cluster builds it and writes the whole table
       if (threadIdx.x == 0) {
-        const int c = cap <= HUB_CL_SLOTS ? 0 : cap <= 2 * HUB_CL_SLOTS ? 1 : cap <= 4 * HUB_CL_SLOTS ? 2 : 3;
+        const int c = cap <= HUB_CL1_SLOTS ? 0 : cap <= 2 * HUB_CL_SLOTS ? 1 : cap <= 4 * HUB_CL_SLOTS ? 2 : 3;
         s.hub_used[h] = 0;
         s.hub_rb[h] = HUB_REBUILD;  // cleared by the cluster once built
         s.hub_cl[(int64_t)c * s.nhubs + (int64_t)atomicAdd(&s.hub_ccnt[c], 1ull)] = h;
@@ -826,7 +828,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
 
 constexpr int HUB_NT = 512;
 
-// A hub table of at most C x HUB_CL_SLOTS packed slots is rebuilt from the
+// A hub table of at most C x hub_cl_slots(C) packed slots is rebuilt from the
 // hub's row by a cluster of C CTAs: the table is laid out in its final hash
 // order across the cluster's shared memories (CTA p holds slots
 // [p S, (p+1) S)), every arc's label is added there with shared-memory
@@ -834,7 +836,7 @@ constexpr int HUB_NT = 512;
 // writes its part with coalesced stores. No global atomics.
 template <class W, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_cl(ScanCtx s) {
-  extern __shared__ __align__(16) unsigned long long T[];  // HUB_CL_SLOTS
+  extern __shared__ __align__(16) unsigned long long T[];  // hub_cl_slots(C)
   __shared__ unsigned long long st_w[HUB_NT / 32][32];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -849,7 +851,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
     const int64_t S = (cap + C - 1) / C;  // slots per CTA
     const int64_t mine = cap - rank * S < S ? cap - rank * S : S;
     for (int64_t i = threadIdx.x; i < S; i += HUB_NT) T[i] = SLOT_EMPTY;
-    cl.sync();  // every part is cleared before any insert
+    if constexpr (C == 1) __syncthreads(); else cl.sync();  // every part is cleared before any insert
     const int64_t beg = s.off[v], end = s.off[v + 1];
     const int64_t share = (end - beg + C - 1) / C;
     const int64_t a0 = beg + rank * share, a1 = a0 + share < end ? a0 + share : end;
@@ -885,28 +887,44 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
           // slot = owner * S + local (tables here are < 2^32 slots); probing steps local
           // and carries into the next owner, wrapping at cap
           const uint32_t home = (uint32_t)hub_home(lbl[j], cap);
-          uint32_t owner = home / (uint32_t)S, local = home - owner * (uint32_t)S;
-          for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
-            unsigned long long* p = C == 1 ? T + local : cl.map_shared_rank(T + local, owner);
-            const unsigned long long prev = atomicCAS(p, SLOT_EMPTY, x);
-            if (prev == SLOT_EMPTY) {
-              ++claimed;
-              break;
+          if constexpr (C == 1) {  // the whole table is local
+            uint32_t slot = home;
+            for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
+              const unsigned long long prev = atomicCAS(&T[slot], SLOT_EMPTY, x);
+              if (prev == SLOT_EMPTY) {
+                ++claimed;
+                break;
+              }
+              if ((int32_t)(prev >> 32) == lbl[j]) {
+                atomicAdd(&T[slot], sum);
+                break;
+              }
+              slot = slot + 1 == (uint32_t)cap ? 0 : slot + 1;
             }
-            if ((int32_t)(prev >> 32) == lbl[j]) {
-              atomicAdd(p, sum);
-              break;
-            }
-            if (++local == (uint32_t)S || (int64_t)owner * S + local == cap) {
-              local = 0;
-              owner = (int64_t)(owner + 1) * S >= cap ? 0 : owner + 1;
+          } else {
+            uint32_t owner = home / (uint32_t)S, local = home - owner * (uint32_t)S;
+            for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
+              unsigned long long* p = cl.map_shared_rank(T + local, owner);
+              const unsigned long long prev = atomicCAS(p, SLOT_EMPTY, x);
+              if (prev == SLOT_EMPTY) {
+                ++claimed;
+                break;
+              }
+              if ((int32_t)(prev >> 32) == lbl[j]) {
+                atomicAdd(p, sum);
+                break;
+              }
+              if (++local == (uint32_t)S || (int64_t)owner * S + local == cap) {
+                local = 0;
+                owner = (int64_t)(owner + 1) * S >= cap ? 0 : owner + 1;
+              }
             }
           }
         }
         __syncwarp();
       }
     }
-    cl.sync();  // every insert is done
+    if constexpr (C == 1) __syncthreads(); else cl.sync();  // every insert is done
     for (int64_t i = threadIdx.x; i < mine; i += HUB_NT) s.hub_slot[base + rank * S + i] = T[i];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULL, claimed, o);
@@ -916,7 +934,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
       atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - beg));
       atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
     }
-    cl.sync();  // the parts are written before they are cleared for the next hub
+    if constexpr (C == 1) __syncthreads(); else cl.sync();  // parts written before the next hub clears them
   }
 }
 constexpr int HUB_CAP = 2 * HUB_CHUNK;
@@ -1380,10 +1398,10 @@ int set_smem_attrs() {
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_CL_SMEM));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(1)));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(2)));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(4)));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(8)));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
   done = true;
@@ -1413,10 +1431,10 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
-      CD_LAUNCH((k_hub_build_cl<W, 1><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 8><<<304, HUB_NT, HUB_CL_SMEM, st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 1><<<456, HUB_NT, hub_cl_smem(1), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, hub_cl_smem(2), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, hub_cl_smem(4), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 8><<<304, HUB_NT, hub_cl_smem(8), st>>>(s)));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
