@@ -397,6 +397,13 @@ __global__ void __launch_bounds__(NT) k_ag_compact(const int64_t* __restrict__ s
 
 }  // namespace
 
+// Inside aggregate_hash: a CUDA error frees the scratch before returning.
+#define AG_CHECK(call)                                         \
+  do {                                                         \
+    cudaError_t _e = (call);                                   \
+    if (_e != cudaSuccess) return fail(set_cuda_error(_e));    \
+  } while (0)
+
 int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, int64_t k,
                    cd_graph** coarse_out) {
   cudaStream_t s = g->stream;
@@ -449,7 +456,7 @@ int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_
     if (n > 0) CD_LAUNCH(k_ag_mdeg<<<gcap((n + NT - 1) / NT), NT, 0, s>>>(g->off, sv, n, mpre));
     if ((rc = exclusive_scan_i64(mpre, mpre, n, tot, s))) return fail(rc);
     if (n > 0) CD_LAUNCH(k_ag_heads<<<gcap((n + NT - 1) / NT), NT, 0, s>>>(sk, mpre, n, sstart));
-    CD_CHECK(cudaMemcpyAsync(sstart + k, tot, 8, cudaMemcpyDeviceToDevice, s));
+    AG_CHECK(cudaMemcpyAsync(sstart + k, tot, 8, cudaMemcpyDeviceToDevice, s));
     if (m > 0) {
       const unsigned gr = gcap((n + NW - 1) / NW);
       if (g->wkind == W_UNIT)
@@ -473,57 +480,57 @@ int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_
     KTimer t(g, K_AGG_REDUCE, (double)m * 2 * (4 + 8) + (double)k * 32);
     // 3: classes
     unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    CD_CHECK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+    AG_CHECK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
     if (k > 0) CD_LAUNCH(k_ag_class_count<<<gcap((k + NT - 1) / NT), NT, 0, s>>>(sstart, k, cnt));
-    CD_CHECK(cudaMemcpyAsync(h, cnt, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
-    CD_CHECK(cudaStreamSynchronize(s));
+    AG_CHECK(cudaMemcpyAsync(h, cnt, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    AG_CHECK(cudaStreamSynchronize(s));
     const int64_t nw = (int64_t)h[0], nc = (int64_t)h[1], nl = (int64_t)h[2], nch = (int64_t)h[3];
     if ((rc = dev_alloc_t(&wl, nw, s)) || (rc = dev_alloc_t(&cl, nc, s)) || (rc = dev_alloc_t(&ll, nl, s)) ||
         (rc = dev_alloc_t(&ch_seg, nch, s)) || (rc = dev_alloc_t(&ch_off, nch, s)) || (rc = dev_alloc_t(&dch, nch, s)))
       return fail(rc);
-    CD_CHECK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
+    AG_CHECK(cudaMemsetAsync(cnt, 0, 8 * sizeof(unsigned long long), s));
     if (k > 0) CD_LAUNCH(k_ag_class_fill<<<gcap((k + NT - 1) / NT), NT, 0, s>>>(sstart, k, cnt, wl, cl, ll, ch_seg, ch_off));
     if (nl > 0) {
       if ((rc = dev_alloc_t(&ub, k, s)) || (rc = dev_alloc_t(&tlg, k, s)) || (rc = dev_alloc_t(&toff, k, s)))
         return fail(rc);
-      CD_CHECK(cudaMemsetAsync(ub, 0, k * sizeof(unsigned long long), s));
-      CD_CHECK(cudaMemsetAsync(ucnt, 0, k * sizeof(int64_t), s));  // large segments count by atomics
+      AG_CHECK(cudaMemsetAsync(ub, 0, k * sizeof(unsigned long long), s));
+      AG_CHECK(cudaMemsetAsync(ucnt, 0, k * sizeof(int64_t), s));  // large segments count by atomics
     }
     const size_t wsm = (size_t)NW * AG_WCAP * 12 + (size_t)NW * 32 * 8 + (size_t)NW * AG_WCAP * 2;
     const size_t csm = (size_t)AG_CCAP * 12 + (size_t)(AG_CNT / 32) * 32 * 8 + (size_t)AG_CCAP * 2;
-    CD_CHECK(cudaFuncSetAttribute(k_ag_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
-    CD_CHECK(cudaFuncSetAttribute(k_ag_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
-    CD_CHECK(cudaFuncSetAttribute(k_ag_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+    AG_CHECK(cudaFuncSetAttribute(k_ag_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm));
+    AG_CHECK(cudaFuncSetAttribute(k_ag_cta<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+    AG_CHECK(cudaFuncSetAttribute(k_ag_cta<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
     if (nw > 0) CD_LAUNCH(k_ag_warp<<<gcap((nw + NW - 1) / NW, 152 * 4), NT, wsm, s>>>(sstart, wl, nw, ab, aw, ucnt));
     if (nc > 0)
       CD_LAUNCH(k_ag_cta<false><<<gcap(nc, 152 * 2), AG_CNT, csm, s>>>(sstart, cl, nullptr, nc, ab, aw, ucnt, nullptr, nullptr));
     if (nl > 0) {
       CD_LAUNCH(k_ag_cta<true><<<gcap(nch, 152 * 2), AG_CNT, csm, s>>>(sstart, ch_seg, ch_off, nch, ab, aw, ucnt, dch, ub));
-      CD_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+      AG_CHECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
       CD_LAUNCH(k_ag_tables_size<<<gcap((nl + NT - 1) / NT), NT, 0, s>>>(ll, nl, ub, tlg, toff, cnt));
       unsigned long long slots = 0;
-      CD_CHECK(cudaMemcpyAsync(&slots, cnt, sizeof(slots), cudaMemcpyDeviceToHost, s));
-      CD_CHECK(cudaStreamSynchronize(s));
+      AG_CHECK(cudaMemcpyAsync(&slots, cnt, sizeof(slots), cudaMemcpyDeviceToHost, s));
+      AG_CHECK(cudaStreamSynchronize(s));
       const int64_t nslices = (int64_t)slots / AG_SLICE;
       if ((rc = dev_alloc_t(&gk, (int64_t)slots, s)) || (rc = dev_alloc_t(&gv, (int64_t)slots, s)) ||
           (rc = dev_alloc_t(&owner, nslices, s)))
         return fail(rc);
-      CD_CHECK(cudaMemsetAsync(gk, 0xff, slots * sizeof(int32_t), s));
-      CD_CHECK(cudaMemsetAsync(gv, 0, slots * sizeof(unsigned long long), s));
+      AG_CHECK(cudaMemsetAsync(gk, 0xff, slots * sizeof(int32_t), s));
+      AG_CHECK(cudaMemsetAsync(gv, 0, slots * sizeof(unsigned long long), s));
       CD_LAUNCH(k_ag_tables_own<<<gcap(nl, 152 * 8), NT, 0, s>>>(ll, nl, tlg, toff, owner));
       CD_LAUNCH(k_ag_merge<<<gcap(nch, 152 * 8), NT, 0, s>>>(sstart, ch_seg, ch_off, dch, nch, ab, aw, tlg, toff, gk, gv));
       CD_LAUNCH(k_ag_extract<<<gcap(nslices, 152 * 8), NT, 0, s>>>(owner, nslices, gk, gv, sstart, ab, aw, ucnt));
     }
     // 4: compact into the coarse CSR
     if ((rc = exclusive_scan_i64(ucnt, coff, k, tot, s))) return fail(rc);
-    CD_CHECK(cudaMemcpyAsync(&nseg, tot, 8, cudaMemcpyDeviceToHost, s));
-    CD_CHECK(cudaStreamSynchronize(s));
+    AG_CHECK(cudaMemcpyAsync(&nseg, tot, 8, cudaMemcpyDeviceToHost, s));
+    AG_CHECK(cudaStreamSynchronize(s));
     if ((rc = dev_alloc_t(&coarse_off, k + 1, s)) || (rc = dev_alloc_t(&ccols, nseg + COL_PAD, s)) ||
         (rc = dev_alloc_t(&cw, nseg, s)))
       return fail(rc);
-    CD_CHECK(cudaMemcpyAsync(coarse_off, coff, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-    CD_CHECK(cudaMemcpyAsync(coarse_off + k, tot, 8, cudaMemcpyDeviceToDevice, s));
-    CD_CHECK(cudaMemsetAsync(ccols + nseg, 0, COL_PAD * sizeof(int32_t), s));
+    AG_CHECK(cudaMemcpyAsync(coarse_off, coff, k * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    AG_CHECK(cudaMemcpyAsync(coarse_off + k, tot, 8, cudaMemcpyDeviceToDevice, s));
+    AG_CHECK(cudaMemsetAsync(ccols + nseg, 0, COL_PAD * sizeof(int32_t), s));
     if (k > 0 && nseg > 0)
       CD_LAUNCH(k_ag_compact<<<gcap((k + NW - 1) / NW), NT, 0, s>>>(sstart, ucnt, coff, k, ab, aw, ccols, cw));
     if (cudaGetLastError() != cudaSuccess) return fail(CD_ECUDA);
@@ -536,5 +543,7 @@ int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_
   *coarse_out = c;
   return CD_OK;
 }
+
+#undef AG_CHECK
 
 }  // namespace cd
