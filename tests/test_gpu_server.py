@@ -175,7 +175,9 @@ def test_memory_budget(reqs):
         _check(res, labels, e)
     done.set()
     t.join()
-    assert 0 < peak <= biggest
+    assert peak <= biggest  # (the watcher may miss short admissions; it must never see more)
+    st = srv.stats()
+    assert st["admitted"] == st["completed"] == len(rs) and st["in_use"] == 0
     srv.close()
 
 
