@@ -412,6 +412,7 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
   cd_graph* cur = g;
   int32_t levels = 0;
   int32_t* newid = nullptr;
+  bool settled = false;  // the last level ended with every vertex of `cur` in its own community
   for (int32_t lvl = 0; lvl < p->max_levels && !rc; ++lvl) {
     rc = run_local_move(cur, opts_from(p, lvl), 0, nullptr, nullptr);
     if (rc) break;
@@ -420,7 +421,10 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
     if ((rc = renumber(cur, cur->C, newid, &k))) break;
     if (n0 > 0) CD_LAUNCH(k_compose<<<grid_cap((n0 + NT - 1) / NT), NT, 0, s>>>(labels0, n0, cur->C, newid));
     levels = lvl + 1;
-    if (k == cur->n) break;  // done: every vertex is its own community
+    if (k == cur->n) {  // done: every vertex is its own community
+      settled = true;
+      break;
+    }
     cd_graph* coarse = nullptr;
     rc = aggregate(cur, cur->C, newid, k, &coarse, p->aggregation);
     dev_free(newid, s);
@@ -434,13 +438,30 @@ int cd_louvain_run(cd_graph* g, const cd_params* p, int32_t* labels_out, int on_
     cur = coarse;
   }
   dev_free(newid, s);
+  // Q of the input partition equals Q of the last graph under its final
+  // partition: aggregation keeps every community's volume and internal
+  // weight exactly (integers), so the same quotient follows from a far
+  // smaller graph. That partition is the last local move's if the run settled
+  // there, else (max_levels reached after an aggregation) the coarse
+  // vertices themselves.
+  double q = 0.0;
+  if (!rc) {
+    if (settled) {
+      rc = modularity(cur, cur->C, &q);
+    } else {
+      int32_t* ident = nullptr;
+      if (!(rc = dev_alloc_t(&ident, cur->n, s))) {
+        if (cur->n > 0) CD_LAUNCH(k_iota<<<grid_cap((cur->n + NT - 1) / NT), NT, 0, s>>>(ident, cur->n));
+        rc = modularity(cur, ident, &q);
+        dev_free(ident, s);
+      }
+    }
+  }
   if (cur != g) {
     profile_flush(cur);
     merge_stats(g, cur);
     cd_graph_free(cur);
   }
-  double q = 0.0;
-  if (!rc) rc = modularity(g, labels0, &q);
   if (!rc && n0 > 0)
     if (cudaMemcpyAsync(labels_out, labels0, n0 * 4,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s) != cudaSuccess)
