@@ -46,37 +46,47 @@ def build(force: bool = False) -> str:
 _lib = None
 
 
+def _configure(L):
+    """Declare the C signatures of oracle.h on a loaded library."""
+    L.orc_degw.restype = _I64
+    L.orc_degw.argtypes = [_I64, _P, _P, _P, _P]
+    L.orc_modularity.restype = ctypes.c_double
+    L.orc_modularity.argtypes = [_I64, _P, _P, _P, _P, _P, _P]
+    L.orc_move_gain.restype = None
+    L.orc_move_gain.argtypes = [_I64, _P, _P, _P, _P, _I32, _I32, _P]
+    L.orc_ws_create.restype = _P
+    L.orc_ws_create.argtypes = [_I64]
+    L.orc_ws_free.restype = None
+    L.orc_ws_free.argtypes = [_P]
+    L.orc_lpa_decide.restype = _I32
+    L.orc_lpa_decide.argtypes = [_I64, _P, _P, _P, _P, _I32, _INT, _P]
+    L.orc_louvain_decide.restype = _I32
+    L.orc_louvain_decide.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _I64, _I32, _INT, _P]
+    L.orc_commit.restype = _INT
+    L.orc_commit.argtypes = [_U64, _I32, _I32, _I32]
+    L.orc_lpa.restype = _I32
+    L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P, _P]
+    L.orc_local_move.restype = _I32
+    L.orc_local_move.argtypes = [_I64, _P, _P, _P, _I32, _INT, _INT, _U64, _I32, _INT, _P, _P,
+                                 _P, _P, _P, _P, _P]
+    L.orc_aggregate.restype = _I64
+    L.orc_aggregate.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+    L.orc_louvain.restype = _I32
+    L.orc_louvain.argtypes = [_I64, _P, _P, _P, _I32, _I32, _INT, _INT, _U64, _P, _P, _P, _P, _P]
+    return L
+
+
+def load(path: str):
+    """Load and configure an oracle library built from ``oracle.c`` at `path`
+    (the tests load deliberately altered copies this way)."""
+    return _configure(ctypes.CDLL(path))
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = ctypes.CDLL(_LIB)
-        L.orc_degw.restype = _I64
-        L.orc_degw.argtypes = [_I64, _P, _P, _P, _P]
-        L.orc_modularity.restype = ctypes.c_double
-        L.orc_modularity.argtypes = [_I64, _P, _P, _P, _P, _P, _P]
-        L.orc_move_gain.restype = None
-        L.orc_move_gain.argtypes = [_I64, _P, _P, _P, _P, _I32, _I32, _P]
-        L.orc_ws_create.restype = _P
-        L.orc_ws_create.argtypes = [_I64]
-        L.orc_ws_free.restype = None
-        L.orc_ws_free.argtypes = [_P]
-        L.orc_lpa_decide.restype = _I32
-        L.orc_lpa_decide.argtypes = [_I64, _P, _P, _P, _P, _I32, _INT, _P]
-        L.orc_louvain_decide.restype = _I32
-        L.orc_louvain_decide.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _I64, _I32, _INT, _P]
-        L.orc_commit.restype = _INT
-        L.orc_commit.argtypes = [_U64, _I32, _I32, _I32]
-        L.orc_lpa.restype = _I32
-        L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P, _P]
-        L.orc_local_move.restype = _I32
-        L.orc_local_move.argtypes = [_I64, _P, _P, _P, _I32, _INT, _INT, _U64, _I32, _INT, _P, _P,
-                                     _P, _P, _P, _P, _P]
-        L.orc_aggregate.restype = _I64
-        L.orc_aggregate.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]
-        L.orc_louvain.restype = _I32
-        L.orc_louvain.argtypes = [_I64, _P, _P, _P, _I32, _I32, _INT, _INT, _U64, _P, _P, _P, _P, _P]
-        _lib = L
+        _lib = load(_LIB)
     return _lib
 
 
