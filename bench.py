@@ -67,7 +67,15 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="override the R-MAT scale")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-arcs", type=float, default=2e8)
+    ap.add_argument("--cpu-sample-arcs", type=float, default=2e8,
+                    help="arcs per round of the oracle sample timed for cpu_baseline (about 20 s)")
+    ap.add_argument("--ref-sample-arcs", type=float, default=2e7,
+                    help="--impl reference: arcs per round of the oracle sample of each step (about 2 s)")
+    ap.add_argument("--no-many", action="store_true",
+                    help="R-MAT line only: skip the batched and served parts of the metric")
+    ap.add_argument("--many-steps", type=int, default=3, help="timed steps of the batched and served parts")
+    ap.add_argument("--served-in-line", type=int, default=256,
+                    help="requests of the 20,000-request stream run in the R-MAT line's served part")
     ap.add_argument("--json-out", default=None)
     ap.add_argument("--asynchronous", action="store_true",
                     help="the asynchronous variant (moves take effect at once; not reproducible)")
@@ -121,6 +129,22 @@ def allreduce_sum(x: float, world: int) -> float:
 def job_rate(units: float, seconds: float, world: int) -> float:
     """Whole-job throughput of replicas: the units of all ranks over the slowest rank's time."""
     return allreduce_sum(float(units), world) / allreduce_max(float(seconds), world)
+
+
+# the schedule parameters every timed run uses (cd_params_default)
+RUN_PARAMS = {"max_iter": 100, "max_levels": 64, "threshold": 0}
+
+
+def graph_config(args, scale, n, nnz, world):
+    """The workload description both arms report."""
+    return {"workload": f"{args.workload}" + (f"_scale{scale}" if scale else ""),
+            "description": WORKLOADS[args.workload], "n": n, "arcs": nnz,
+            "l2": "inputs larger than L2 (column array %.1f GB)" % (nnz * 4 / 1e9),
+            "parallelism": f"replicas x{world}",
+            "schedule": ("asynchronous rounds (moves applied at once), " if args.asynchronous else
+                         "synchronous rounds, ") + "SplitMix64 deferral coin, strict-positive gain, "
+                        "smallest-id ties, singleton rule",
+            **RUN_PARAMS, "asynchronous": bool(args.asynchronous)}
 
 
 def make_graph(name: str, scale_override, device: str):
@@ -200,8 +224,49 @@ def run_step(cd, g_dev, params, labels_lpa, labels_lv, host=False, g_host=None):
     info = {"lpa_rounds": rounds, "louvain_levels": levels, "louvain_rounds": len(tr_lv), "q": q,
             "lpa_arcs": sum(t["arcs"] for t in tr_lpa), "louvain_arcs": sum(t["arcs"] for t in tr_lv),
             "lpa_scan_ms": sum(t["scan_ms"] for t in tr_lpa),
-            "louvain_scan_ms": sum(t["scan_ms"] for t in tr_lv)}
-    return arcs, info, prof_lpa + prof_lv
+            "louvain_scan_ms": sum(t["scan_ms"] for t in tr_lv),
+            "lpa_hit_max_iter": bool(rounds == params.max_iter and tr_lpa and
+                                     tr_lpa[-1]["moved"] + tr_lpa[-1]["deferred"] > params.threshold),
+            "louvain_levels_detail": level_summary(tr_lv, params.max_iter)}
+    return arcs, info, prof_lpa + prof_lv, (tr_lpa, tr_lv)
+
+
+def level_summary(tr_lv, max_iter):
+    """Per Louvain level: rounds, arcs scanned, moves, and whether the level
+    stopped at max_iter with vertices still wanting to move."""
+    out = []
+    for lv in sorted({t["level"] for t in tr_lv}):
+        rows = [t for t in tr_lv if t["level"] == lv]
+        out.append({"level": lv, "rounds": len(rows), "arcs": sum(t["arcs"] for t in rows),
+                    "moved": sum(t["moved"] for t in rows),
+                    "hit_max_iter": bool(len(rows) == max_iter and rows[-1]["moved"] + rows[-1]["deferred"] > 0)})
+    return out
+
+
+def round_bytes(t, louv: bool, wbytes: int, n: int) -> float:
+    """Algorithmic bytes of one scan round of the method (independent of how
+    the kernels organise the work): per examined vertex its offsets (8), label
+    (4), label write (4) and flag (1); per scanned arc its column (4), the
+    neighbour's label (4) and weight (wbytes); marking the neighbours of moved
+    vertices (4 per arc of a moved vertex) and clearing n next-round flags.
+    Louvain adds the Sigma_tot gather of every candidate pair (8), deg_w of
+    every examined vertex (8) and the Sigma_tot/size updates of every move (24)."""
+    b = t["arcs"] * (8 + wbytes) + t["active"] * 17 + 4 * t["moved_arcs"] + n
+    if louv:
+        b += 8 * t["cands"] + 8 * t["active"] + 24 * t["moved"]
+    return float(b)
+
+
+def round_figures(rows, louv, wbytes, n, peak):
+    """Median over steps of one round's device time, with its GTEPS and
+    algorithmic GB/s against the HBM peak."""
+    ms = statistics.median(t["round_ms"] for t in rows)
+    scan_ms = statistics.median(t["scan_ms"] for t in rows)
+    t = rows[-1]
+    b = round_bytes(t, louv, wbytes, n)
+    return {"ms": ms, "scan_ms": scan_ms, "active": t["active"], "arcs": t["arcs"], "cands": t["cands"],
+            "moved": t["moved"], "moved_arcs": t["moved_arcs"], "gteps": t["arcs"] / (ms / 1e3) / 1e9,
+            "alg_bytes": b, "GBps": b / (ms / 1e3) / 1e9, "frac": b / (ms / 1e3) / 1e9 / peak}
 
 
 def merge_profiles(acc: dict, prof: list):
@@ -284,7 +349,7 @@ def run_reference(args, rank, world):
     del g
     samples = []
     for i in range(args.warmup + args.steps):
-        arcs, dt, desc = oracle_sample(off, cols, w, args.cpu_sample_arcs)
+        arcs, dt, desc = oracle_sample(off, cols, w, args.ref_sample_arcs)
         if i >= args.warmup:
             samples.append((arcs, dt))
     arcs = sum(a for a, _ in samples)
@@ -294,9 +359,7 @@ def run_reference(args, rank, world):
             "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, len(samples)),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": {"workload": f"{args.workload}" + (f"_scale{scale}" if scale else ""),
-                                            "description": WORKLOADS[args.workload],
-                                            "n": len(off) - 1, "arcs": int(off[-1])},
+            "data": "synthetic", "config": graph_config(args, scale, len(off) - 1, int(off[-1]), world),
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -404,7 +467,7 @@ def serve_requests(workload: str, seed: int, count: int = 0):
     return [_host_req(1 if kinds[i] == 0 else 2, graphs[o]) for i, o in enumerate(order)]
 
 
-def run_serve(args, rank, world, local):
+def run_serve(args, rank, world, local, steps=None, warmup=None, workload=None, requests=None):
     """Requests through the serving engine (continuous batching over worker
     streams) vs the same requests one call at a time: throughput when all
     arrive at once, and latency under Poisson arrivals at 0.8x the measured
@@ -417,7 +480,10 @@ def run_serve(args, rank, world, local):
     import paper_2507_06471_gb300 as cd
 
     cd.lib()
-    reqs = serve_requests(args.workload, 11 + 7919 * rank, args.serve_requests)
+    steps = steps if steps is None else steps
+    warmup = warmup if warmup is None else warmup
+    workload = workload or args.workload
+    reqs = serve_requests(workload, 11 + 7919 * rank, requests or args.serve_requests)
     torch.cuda.synchronize()
     torch.cuda.empty_cache()
     R = len(reqs)
@@ -456,7 +522,7 @@ def run_serve(args, rank, world, local):
     small_n, batch_arcs = 8192, 1 << 22
     srv = cd.Server(slots=args.serve_slots, small_n=small_n, batch_arcs=batch_arcs)
     seq = cd.Server(slots=1, small_n=0)
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         burst(srv)
     # one call at a time: capacity and labels
     seq_s, seq_out = burst(seq)
@@ -469,7 +535,7 @@ def run_serve(args, rank, world, local):
     launches0 = cd.cd_launch_count()
     secs, lat, packed = [], [], []
     last = None
-    for _ in range(args.steps):
+    for _ in range(steps):
         dt, last = burst(srv)
         secs.append(dt)
         lat += [r.latency_ms for _, r in last]
@@ -479,7 +545,7 @@ def run_serve(args, rank, world, local):
     launches = cd.cd_launch_count() - launches0
     clk = clocks.stop()
     wall = allreduce_max(sum(secs), world)
-    value = allreduce_sum(float(R * args.steps), world) / wall
+    value = allreduce_sum(float(R * steps), world) / wall
     stats = srv.stats()
     same = all(np.array_equal(a[0], b[0]) and a[1].iters == b[1].iters for a, b in zip(seq_out, last))
 
@@ -490,10 +556,10 @@ def run_serve(args, rank, world, local):
     seq.close()
 
     line = {"metric": METRIC_SERVE,
-            "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+            "value": value, "unit": "requests/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": 1e3 * wall / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "requests": R,
+            "config": {"workload": workload, "description": WORKLOADS[workload], "requests": R,
                        "arcs": arcs, "slots": args.serve_slots, "small_n": small_n, "batch_arcs": batch_arcs,
                        "parallelism": f"replicas x{world}",
                        "timing": "host wall clock from the first submit to the last result; all requests "
@@ -508,16 +574,12 @@ def run_serve(args, rank, world, local):
             "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "note": "the value itself is end to end: host buffers in, host labels out"},
             "gpu_launches": launches, "clocks": clk}
-    if rank == 0:
-        print(json.dumps(line))
-        if args.json_out:
-            with open(args.json_out, "w") as f:
-                json.dump(line, f, indent=1)
+    return line
 
 
 # ------------------------------------------------------------------ batched workload
 
-def run_batch(args, rank, world, local):
+def run_batch(args, rank, world, local, steps=None, warmup=None):
     """Louvain on 4,096 graphs at once (batched mode) vs one call per graph."""
     import numpy as np
     import torch
@@ -526,6 +588,8 @@ def run_batch(args, rank, world, local):
     import synth
 
     cd.lib()
+    steps = steps if steps is None else steps
+    warmup = warmup if warmup is None else warmup
     specs = synth.batch_specs(4096, seed=4 + 4096 * rank)
     g, vstart, _ = synth.sbm_batch_device(specs)
     torch.cuda.synchronize()
@@ -551,7 +615,7 @@ def run_batch(args, rank, world, local):
         cd.cd_graph_free(h)
         return sum(t["arcs"] for t in tr), len(tr), levels, q, prof
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     clocks = ClockSampler(local)
     barrier(world)
@@ -562,7 +626,7 @@ def run_batch(args, rank, world, local):
     ev0.record(stream)
     arcs = 0
     prof = {}
-    for _ in range(args.steps):
+    for _ in range(steps):
         a, rounds, levels, q, p = step(timing=True)
         arcs += a
         merge_profiles(prof, p)
@@ -572,7 +636,7 @@ def run_batch(args, rank, world, local):
     launches = cd.cd_launch_count() - launches0
     clk = clocks.stop()
     ms = allreduce_max(ev0.elapsed_time(ev1), world)
-    graphs_per_s = allreduce_sum(float(B * args.steps), world) / (ms / 1e3)
+    graphs_per_s = allreduce_sum(float(B * steps), world) / (ms / 1e3)
 
     # one call per graph (upload + cd_louvain_run) on an evenly spaced sample
     members = synth.unpack_batch(g, vstart)
@@ -602,8 +666,8 @@ def run_batch(args, rank, world, local):
                    "share": round(v["total_ms"] / total_prof_ms, 4) if total_prof_ms else 0}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]) if v["launches"]}
     line = {"metric": METRIC_BATCH,
-            "value": graphs_per_s, "unit": "graphs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "value": graphs_per_s, "unit": "graphs/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "batch4096", "description": WORKLOADS["batch4096"], "graphs": B,
                        "n": g.n, "arcs": g.nnz, "parallelism": f"replicas x{world}",
@@ -614,6 +678,12 @@ def run_batch(args, rank, world, local):
                      "how": "cd_csr_upload + cd_louvain_run per graph, one graph at a time"},
             "speedup_vs_solo": graphs_per_s / solo_gps, "kernels": kernels, "gpu_launches": launches,
             "clocks": clk}
+    return line
+
+
+# ------------------------------------------------------------------ main
+
+def emit(line, args, rank):
     if rank == 0:
         print(json.dumps(line))
         if args.json_out:
@@ -621,7 +691,13 @@ def run_batch(args, rank, world, local):
                 json.dump(line, f, indent=1)
 
 
-# ------------------------------------------------------------------ main
+def compact_many(line):
+    """The parts of a batched or served line carried inside the R-MAT line."""
+    keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "config", "gteps",
+            "louvain_rounds", "mean_q", "solo", "speedup_vs_solo", "latency_ms_all_at_once", "open_loop",
+            "mean_batched_with", "one_at_a_time", "speedup_vs_one_at_a_time", "e2e", "gpu_launches", "clocks")
+    return {k: line[k] for k in keep if k in line}
+
 
 def main():
     args = parse()
@@ -630,11 +706,28 @@ def main():
         run_reference(args, rank, world)
         return
     if args.workload == "batch4096":
-        run_batch(args, rank, world, local)
+        emit(run_batch(args, rank, world, local), args, rank)
         return
     if args.workload in ("serve2048", "served"):
-        run_serve(args, rank, world, local)
+        emit(run_serve(args, rank, world, local), args, rank)
         return
+    line = run_graph(args, rank, world, local)
+    if args.workload == "rmat26" and args.scale is None and not args.no_many:
+        # the batched and served parts of the metric, each timed on its own
+        ms, wu = args.many_steps, min(args.warmup, 2)
+        line["batch4096"] = compact_many(run_batch(args, rank, world, local, steps=ms, warmup=wu))
+        line["serve2048"] = compact_many(run_serve(args, rank, world, local, steps=ms, warmup=wu,
+                                                   workload="serve2048"))
+        line["served"] = compact_many(run_serve(args, rank, world, local, steps=1, warmup=1, workload="served",
+                                                requests=args.served_in_line))
+    emit(line, args, rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_graph(args, rank, world, local):
+    """One graph: upload + LPA + Louvain per step (the headline GTEPS line)."""
     import numpy as np
     import torch
 
@@ -646,9 +739,11 @@ def main():
     torch.cuda.synchronize()
     torch.cuda.empty_cache()  # hand the generator's scratch back before the library allocates
     n, nnz = g.n, g.nnz
+    wbytes = 0 if g.w is None else 4
     labels_lpa = torch.empty(n, dtype=torch.int32, device="cuda")
     labels_lv = torch.empty(n, dtype=torch.int32, device="cuda")
     params = cd.cd_params_default(asynchronous=int(args.asynchronous))
+    assert {k: getattr(params, k) for k in RUN_PARAMS} == RUN_PARAMS
     stream = torch.cuda.current_stream()
 
     # warm-up (untimed)
@@ -668,10 +763,12 @@ def main():
     total_arcs = 0
     infos = []
     prof = {}
+    traces = []
     for _ in range(args.steps):
-        arcs, info, p = run_step(cd, g, params, labels_lpa, labels_lv)
+        arcs, info, p, tr = run_step(cd, g, params, labels_lpa, labels_lv)
         total_arcs += arcs
         infos.append(info)
+        traces.append(tr)
         merge_profiles(prof, p)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -697,7 +794,7 @@ def main():
         t0 = time.perf_counter()
         e2e_arcs = 0
         for _ in range(args.e2e_steps):
-            a, _, _ = run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
+            a, _, _, _ = run_step(cd, None, params_e2e, lab_h1, lab_h2, host=True, g_host=(off_h, cols_h, w_h))
             e2e_arcs += a
         torch.cuda.synchronize()
         e2e_s = allreduce_max(time.perf_counter() - t0, world)
@@ -718,23 +815,35 @@ def main():
                    "GBps": round(v["alg_bytes"] / (v["total_ms"] / 1e3) / 1e9, 1) if v["total_ms"] else 0}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["total_ms"]) if v["launches"]}
 
+    # the method's per-round figures: the first LPA round and the first
+    # local-moving round of level 0 (every vertex examined), median over steps
+    lpa0 = [tr[0][0] for tr in traces if tr[0]]
+    lv0 = [tr[1][0] for tr in traces if tr[1]]
+    rounds = {"bytes": "per round: arcs x (column 4 + neighbour label 4 + weight) + examined vertices x 17 "
+                       "(offsets, label, label write, flag) + 4 x arcs of moved vertices + n flag clears; "
+                       "Louvain adds 8 per candidate pair, 8 per examined vertex, 24 per move",
+              "time": "CUDA events on the library stream from the round's first to its last kernel "
+                      "(scan_ms: up to the end of the scan kernels)",
+              "peak": peak}
+    if lpa0:
+        rounds["lpa_round0"] = round_figures(lpa0, False, wbytes, n, peak)
+    if lv0:
+        rounds["louvain_level0_round0"] = round_figures(lv0, True, wbytes, n, peak)
+
     line = {
         "metric": METRIC_GTEPS,
         "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": wl_name, "description": WORKLOADS[args.workload], "n": n, "arcs": nnz,
-                   "l2": "inputs larger than L2 (column array %.1f GB)" % (nnz * 4 / 1e9),
-                   "parallelism": f"replicas x{world}", "schedule": ("asynchronous rounds (moves applied at once), " if args.asynchronous else "synchronous rounds, ") + "SplitMix64 "
-                   "deferral coin, strict-positive gain, smallest-id ties, singleton rule",
-                   "max_iter": params.max_iter, "max_levels": params.max_levels,
-                   "threshold": params.threshold, "asynchronous": bool(args.asynchronous)},
+        "config": graph_config(args, scale, n, nnz, world),
         "time_to_converge_ms": {"lpa_plus_louvain_step": ms_max / args.steps},
         "step": infos[-1],
+        "rounds": rounds,
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / max(1, args.e2e_steps)},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
+                     "bytes": "library-counted algorithmic bytes of the kernel (per-kernel table of the design notes)",
                      "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "kernels": kernels,
         "gpu_launches": launches,
@@ -746,14 +855,10 @@ def main():
         arcs, dt, desc = oracle_sample(off, cols, w, args.cpu_sample_arcs)
         line["cpu_baseline"] = {"value": arcs / dt / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                                 "sample": desc, "seconds": dt}
-    if rank == 0:
-        print(json.dumps(line))
-        if args.json_out:
-            with open(args.json_out, "w") as f:
-                json.dump(line, f, indent=1)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    del g, off_h, cols_h, w_h, lab_h1, lab_h2, labels_lpa, labels_lv
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return line
 
 
 if __name__ == "__main__":

@@ -80,6 +80,8 @@ typedef struct cd_round_trace {
   int64_t deferred; /* vertices whose move was deferred by the coin */
   float scan_ms;    /* device time of the scan kernels (timing = 1) */
   float round_ms;   /* device time of the whole round (timing = 1) */
+  int64_t cands;    /* candidate pairs: distinct neighbour labels (own one included) summed over examined vertices */
+  int64_t moved_arcs; /* arcs of the vertices that moved (their neighbours are flagged) */
 } cd_round_trace;
 
 /* Per-kernel totals of the last run (cd_profile_get; timing = 1). */
@@ -276,9 +278,11 @@ int64_t cd_launch_count(void);
  * *q_out is written. Scratch is a static device array inside the library
  * (16 MiB, held by every GPU that loads the library until exit), so n may be
  * at most 2,097,152; larger n gives CD_EINVAL. The first call on each device
- * looks the array's device address up (with that device current), so make it
- * before any stream capture. All calls share the array: calls that overlap
- * on the GPU race and must not be issued. Errors: CD_EINVAL (null pointer, n
+ * looks the array's device address up and loads this entry point's kernels
+ * (with that device current), so make it before any stream capture; the kept
+ * address belongs to the device's primary context, so the library must not
+ * be used after cudaDeviceReset. All calls share the array: calls that
+ * overlap on the GPU race and must not be issued. Errors: CD_EINVAL (null pointer, n
  * too large, label outside [0, n), weight < 1), CD_EBOUNDS (column outside
  * [0, n)), CD_ENOTSYM (offsets outside [0, nnz] or decreasing), CD_ECUDA. */
 int cd_modularity_noalloc(const int64_t* off, const int32_t* cols, const int32_t* w,

@@ -65,10 +65,10 @@ def _configure(L):
     L.orc_commit.restype = _INT
     L.orc_commit.argtypes = [_U64, _I32, _I32, _I32]
     L.orc_lpa.restype = _I32
-    L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P, _P]
+    L.orc_lpa.argtypes = [_I64, _P, _P, _P, _I32, _I64, _INT, _INT, _U64, _P, _P, _P, _P, _P, _P, _P, _P]
     L.orc_local_move.restype = _I32
     L.orc_local_move.argtypes = [_I64, _P, _P, _P, _I32, _INT, _INT, _U64, _I32, _INT, _P, _P,
-                                 _P, _P, _P, _P, _P]
+                                 _P, _P, _P, _P, _P, _P, _P]
     L.orc_aggregate.restype = _I64
     L.orc_aggregate.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]
     L.orc_louvain.restype = _I32
@@ -179,10 +179,12 @@ class RunTrace:
     deferred: np.ndarray
     active: np.ndarray
     arcs: np.ndarray
+    cands: np.ndarray       # distinct neighbour labels summed over the examined vertices
+    moved_arcs: np.ndarray  # arcs of the vertices that moved
 
 
-def _trace(r, tm, td, ta, tr):
-    return RunTrace(int(r), tm[:r].copy(), td[:r].copy(), ta[:r].copy(), tr[:r].copy())
+def _trace(r, *arrays):
+    return RunTrace(int(r), *(a[:r].copy() for a in arrays))
 
 
 def _active(a):
@@ -198,11 +200,11 @@ def lpa(off, cols, w=None, max_iter=100, threshold=0, tie_keep_current=1, use_fr
     n = len(off) - 1
     labels = np.zeros(n, dtype=np.int32)
     cap = max(max_iter, 1)
-    tm, td, ta, tr = (np.zeros(cap, dtype=np.int64) for _ in range(4))
+    tm, td, ta, tr, tc, tk = (np.zeros(cap, dtype=np.int64) for _ in range(6))
     r = lib().orc_lpa(n, _ptr(off), _ptr(cols), _ptr(w), max_iter, threshold, tie_keep_current,
                       use_frontier, sched_seed, _ptr(active_in), _ptr(labels), _ptr(tm), _ptr(td),
-                      _ptr(ta), _ptr(tr))
-    return labels, _trace(r, tm, td, ta, tr)
+                      _ptr(ta), _ptr(tr), _ptr(tc), _ptr(tk))
+    return labels, _trace(r, tm, td, ta, tr, tc, tk)
 
 
 def local_move(off, cols, w=None, max_iter=100, singleton_rule=1, use_frontier=1, labels_in=None,
@@ -219,14 +221,14 @@ def local_move(off, cols, w=None, max_iter=100, singleton_rule=1, use_frontier=1
         labels = np.ascontiguousarray(labels_in, dtype=np.int32).copy()
         given = 1
     cap = max(max_iter, 1)
-    tm, td, ta, tr = (np.zeros(cap, dtype=np.int64) for _ in range(4))
+    tm, td, ta, tr, tc, tk = (np.zeros(cap, dtype=np.int64) for _ in range(6))
     moves = np.zeros(1, dtype=np.int64)
     r = lib().orc_local_move(n, _ptr(off), _ptr(cols), _ptr(w), max_iter, singleton_rule, use_frontier,
                              sched_seed, level, given, _ptr(active_in), _ptr(labels), _ptr(moves),
-                             _ptr(tm), _ptr(td), _ptr(ta), _ptr(tr))
+                             _ptr(tm), _ptr(td), _ptr(ta), _ptr(tr), _ptr(tc), _ptr(tk))
     if r < 0:
         raise ValueError("labels out of range")
-    return labels, int(moves[0]), _trace(r, tm, td, ta, tr)
+    return labels, int(moves[0]), _trace(r, tm, td, ta, tr, tc, tk)
 
 
 def aggregate(off, cols, w, labels):

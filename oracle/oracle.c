@@ -183,6 +183,15 @@ static void reset(orc_ws* ws) {
   ws->ntouched = 0;
 }
 
+/* number of distinct labels among v's neighbours (loops excluded) */
+static int64_t distinct_labels(const int64_t* off, const int32_t* cols,
+                               const int32_t* labels, int32_t v, orc_ws* ws) {
+  accumulate(off, cols, NULL, labels, v, ws);
+  int64_t k = ws->ntouched;
+  reset(ws);
+  return k;
+}
+
 /* ---- Algorithm 1, PLPMove: most frequent (heaviest) neighbour label --- */
 
 int32_t orc_lpa_decide(int64_t n, const int64_t* off, const int32_t* cols,
@@ -285,7 +294,7 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
                 int tie_keep_current, int use_frontier, uint64_t sched_seed,
                 const unsigned char* active_in, int32_t* labels_out,
                 int64_t* tr_moved, int64_t* tr_deferred, int64_t* tr_active,
-                int64_t* tr_arcs) {
+                int64_t* tr_arcs, int64_t* tr_cands, int64_t* tr_marcs) {
   int32_t* C = labels_out;
   int32_t* nxt = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
   unsigned char* active = (unsigned char*)malloc((size_t)n + 1);
@@ -299,13 +308,14 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
     memset(active, 1, (size_t)n);                     /* V_active = V */
   int32_t rounds = 0;
   for (int32_t r = 0; r < max_iter; ++r) {
-    int64_t nact = 0, arcs = 0, nmoved = 0, ndef = 0;
+    int64_t nact = 0, arcs = 0, nmoved = 0, ndef = 0, cands = 0, marcs = 0;
     memset(deferred, 0, (size_t)n);
     for (int64_t v = 0; v < n; ++v) {
       nxt[v] = C[v];
       if (!active[v]) continue;
       ++nact;
       arcs += off[v + 1] - off[v];
+      if (tr_cands) cands += distinct_labels(off, cols, C, (int32_t)v, ws);
       int32_t c = orc_lpa_decide(n, off, cols, w, C, (int32_t)v, tie_keep_current, ws);
       if (c == C[v]) continue;
       if (orc_commit(sched_seed, 0, r, (int32_t)v))
@@ -317,9 +327,12 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
       moved[v] = (unsigned char)(nxt[v] != C[v]);
       nmoved += moved[v];
       ndef += deferred[v];
+      if (moved[v]) marcs += off[v + 1] - off[v];
       C[v] = nxt[v];
     }
     mark_next(n, off, cols, moved, deferred, active, use_frontier);
+    if (tr_cands) tr_cands[r] = cands;
+    if (tr_marcs) tr_marcs[r] = marcs;
     if (tr_moved) tr_moved[r] = nmoved;
     if (tr_deferred) tr_deferred[r] = ndef;
     if (tr_active) tr_active[r] = nact;
@@ -343,7 +356,8 @@ int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
                        int init_given, const unsigned char* active_in,
                        int32_t* labels_io, int64_t* moves_out,
                        int64_t* tr_moved, int64_t* tr_deferred,
-                       int64_t* tr_active, int64_t* tr_arcs) {
+                       int64_t* tr_active, int64_t* tr_arcs,
+                       int64_t* tr_cands, int64_t* tr_marcs) {
   int32_t* C = labels_io;
   if (init_given) {
     for (int64_t v = 0; v < n; ++v)
@@ -371,13 +385,14 @@ int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
   int64_t total = 0;
   int32_t rounds = 0;
   for (int32_t r = 0; r < max_iter; ++r) {
-    int64_t nact = 0, arcs = 0, nm = 0, ndef = 0;
+    int64_t nact = 0, arcs = 0, nm = 0, ndef = 0, cands = 0, marcs = 0;
     memset(deferred, 0, (size_t)n);
     for (int64_t v = 0; v < n; ++v) {
       target[v] = C[v];
       if (!flag[v]) continue;
       ++nact;
       arcs += off[v + 1] - off[v];
+      if (tr_cands) cands += distinct_labels(off, cols, C, (int32_t)v, ws);
       int32_t b = orc_louvain_decide(n, off, cols, w, C, sigma, csize, degw, vol,
                                      (int32_t)v, singleton_rule, ws);
       if (b == C[v]) continue;
@@ -398,8 +413,11 @@ int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
       csize[B] += 1;
       C[v] = B;
       ++nm;
+      marcs += off[v + 1] - off[v];
     }
     mark_next(n, off, cols, moved, deferred, flag, use_frontier);
+    if (tr_cands) tr_cands[r] = cands;
+    if (tr_marcs) tr_marcs[r] = marcs;
     if (tr_moved) tr_moved[r] = nm;
     if (tr_deferred) tr_deferred[r] = ndef;
     if (tr_active) tr_active[r] = nact;
@@ -515,7 +533,7 @@ int32_t orc_louvain(int64_t n, const int64_t* off, const int32_t* cols,
     int64_t moves = 0;
     int32_t rounds = orc_local_move(gn, goff, gcols, gw, max_iter, singleton_rule,
                                     use_frontier, sched_seed, lvl, 0, NULL, C,
-                                    &moves, NULL, NULL, NULL, NULL);
+                                    &moves, NULL, NULL, NULL, NULL, NULL, NULL);
     if (tr_rounds) tr_rounds[lvl] = rounds;
     if (tr_moves) tr_moves[lvl] = moves;
     if (tr_nverts) tr_nverts[lvl] = gn;

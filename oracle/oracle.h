@@ -84,7 +84,9 @@ int orc_commit(uint64_t sched_seed, int32_t level, int32_t round, int32_t v);
 /* Algorithm 1 (PLP) with synchronous rounds and the deferral coin.
  * active_in (n bytes, may be NULL = all of V) is the initial V_active.
  * labels_out[n] receives C. Per-round traces (moved, deferred, active
- * vertices, arcs scanned) go to the optional arrays of length max_iter.
+ * vertices, arcs scanned, candidate pairs = distinct neighbour labels summed
+ * over the examined vertices, arcs of the moved vertices) go to the optional
+ * arrays of length max_iter.
  * Stops after a round with moved + deferred <= threshold. Returns the number
  * of rounds. */
 int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
@@ -92,21 +94,24 @@ int32_t orc_lpa(int64_t n, const int64_t* off, const int32_t* cols,
                 int tie_keep_current, int use_frontier, uint64_t sched_seed,
                 const unsigned char* active_in, int32_t* labels_out,
                 int64_t* tr_moved, int64_t* tr_deferred, int64_t* tr_active,
-                int64_t* tr_arcs);
+                int64_t* tr_arcs, int64_t* tr_cands, int64_t* tr_marcs);
 
 /* Algorithm 2 (local moving) with synchronous rounds and the deferral coin of
  * level `level`. If init_given is 0 the partition starts as singletons, else
  * from labels_io (values in [0, n)). active_in (n bytes, may be NULL = all)
  * is the initial needCheck. labels_io[n] receives comID.
- * *moves_out = total moves over all rounds. Stops after a round in which no
- * vertex moved or deferred. Returns the number of rounds (-1: bad labels). */
+ * *moves_out = total moves over all rounds. Per-round traces as for orc_lpa
+ * (candidate pairs count the vertex's own community too). Stops after a round
+ * in which no vertex moved or deferred. Returns the number of rounds (-1: bad
+ * labels). */
 int32_t orc_local_move(int64_t n, const int64_t* off, const int32_t* cols,
                        const int64_t* w, int32_t max_iter, int singleton_rule,
                        int use_frontier, uint64_t sched_seed, int32_t level,
                        int init_given, const unsigned char* active_in,
                        int32_t* labels_io, int64_t* moves_out,
                        int64_t* tr_moved, int64_t* tr_deferred,
-                       int64_t* tr_active, int64_t* tr_arcs);
+                       int64_t* tr_active, int64_t* tr_arcs,
+                       int64_t* tr_cands, int64_t* tr_marcs);
 
 /* Algorithm 3, Aggregation: remap communities to 0..k-1 in ascending id order
  * (newid_out[c], -1 for unused ids) and build the coarse graph whose edge

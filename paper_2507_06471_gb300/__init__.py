@@ -46,7 +46,8 @@ class cd_params(ctypes.Structure):
 class cd_round_trace(ctypes.Structure):
     _fields_ = [("level", ctypes.c_int32), ("round", ctypes.c_int32), ("active", ctypes.c_int64),
                 ("arcs", ctypes.c_int64), ("moved", ctypes.c_int64), ("deferred", ctypes.c_int64),
-                ("scan_ms", ctypes.c_float), ("round_ms", ctypes.c_float)]
+                ("scan_ms", ctypes.c_float), ("round_ms", ctypes.c_float), ("cands", ctypes.c_int64),
+                ("moved_arcs", ctypes.c_int64)]
 
 
 class cd_kernel_profile(ctypes.Structure):

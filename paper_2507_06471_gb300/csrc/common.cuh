@@ -57,6 +57,7 @@ enum Ctr {
   C_BIN0,        // then per bin: active, arcs, candidates
   C_HUB_BARCS = C_BIN0 + 3 * NBINS,  // arcs read by hub table builds this round
   C_HUB_BSLOTS,                      // table slots they (and the clears and compactions) wrote
+  C_MARCS,                           // arcs of the vertices that moved this round
   C_COUNT
 };
 

@@ -9,8 +9,10 @@
 // until the process exits. Host code cannot use the array's name as a device
 // address; on the first call on each device (with that device current) the
 // entry point looks the address up once with cudaGetSymbolAddress and keeps
-// it. That first call should therefore come before any stream capture on the
-// device.
+// it, and loads the entry point's kernels. That first call should therefore
+// come before any stream capture on the device. The kept address belongs to
+// the device's primary context: after cudaDeviceReset the library must not be
+// used again in the process.
 //
 // All calls share the one array and it keeps the previous call's contents, so
 // each call first clears the part it uses. Calls whose work overlaps on the
@@ -32,6 +34,8 @@ constexpr int kMaxDevices = 64;
 unsigned long long* g_scratch_dev[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
+cudaError_t load_kernels();
+
 int scratch_on_current_device(unsigned long long** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -42,6 +46,10 @@ int scratch_on_current_device(unsigned long long** out) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cd::set_cuda_error(e);
+    // With lazy module loading a kernel's code is loaded, which can take
+    // device memory, at its first launch; load all of this entry point's
+    // kernels now so that no later call (weighted or not) loads anything.
+    if ((e = load_kernels()) != cudaSuccess) return cd::set_cuda_error(e);
     g_scratch_dev[dev] = (unsigned long long*)p;
   }
   *out = g_scratch_dev[dev];
@@ -128,6 +136,14 @@ __global__ void __launch_bounds__(NT) k_noalloc_square(int64_t n, unsigned long 
     const unsigned long long carry = old + lo < old ? 1ull : 0ull;
     if (hi + carry) atomicAdd(&ctl[1], hi + carry);
   }
+}
+
+cudaError_t load_kernels() {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, k_noalloc_pass<true>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_noalloc_pass<false>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, k_noalloc_square);
+  return e;
 }
 
 }  // namespace

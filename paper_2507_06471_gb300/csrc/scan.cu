@@ -253,19 +253,21 @@ __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t c
 }
 
 __device__ __forceinline__ void flush_counters(const ScanCtx& s, int bin, int64_t act, int64_t arcs,
-                                               int64_t cands, int64_t def) {
+                                               int64_t cands, int64_t def, int64_t marcs) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     act += __shfl_xor_sync(FULL, act, o);
     arcs += __shfl_xor_sync(FULL, arcs, o);
     cands += __shfl_xor_sync(FULL, cands, o);
     def += __shfl_xor_sync(FULL, def, o);
+    marcs += __shfl_xor_sync(FULL, marcs, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (act) atomicAdd(&s.ctr[C_BIN0 + 3 * bin], (unsigned long long)act);
     if (arcs) atomicAdd(&s.ctr[C_BIN0 + 3 * bin + 1], (unsigned long long)arcs);
     if (cands) atomicAdd(&s.ctr[C_BIN0 + 3 * bin + 2], (unsigned long long)cands);
     if (def) atomicAdd(&s.ctr[C_DEFERRED], (unsigned long long)def);
+    if (marcs) atomicAdd(&s.ctr[C_MARCS], (unsigned long long)marcs);
   }
 }
 
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
   constexpr int VPW = 32 / TILE;
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
-  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
   for (int64_t base = warp * VPW; base < count; base += nwarps * VPW) {
     const int64_t i = base + lane / TILE;
     const bool valid = i < count;
@@ -483,10 +485,11 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
       ++n_act;
       n_arcs += d;
       if (want && !commit) ++n_def;
+      if (commit) n_marcs += d;
     }
-    if (ok) ++n_cand;
+    if (leader) ++n_cand;  // every distinct neighbour label, the vertex's own included
   }
-  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
 // ------------------------------------------------------------------ shared-memory tables
@@ -658,7 +661,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
   }
   if (gl == 0) occ_n[gid] = 0;
   group_sync<GROUP, NTB>(gid);
-  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
   // Software pipeline over the group's vertices: while vertex i is processed,
   // the header of vertex i + stride (activity, row bounds, label, deg_w) and
   // the list entry of vertex i + 2 stride are already in flight.
@@ -724,6 +727,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
       n_def += def;
       ++n_act;
       n_arcs += d;
+      if (target != cur && !def) n_marcs += d;
       occ_n[gid] = 0;
       moved_to[gid] = (target != cur && !def) ? target : -1;
     }
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
         if (s.nhubs > 0 && u != v) hub_neighbour_moved(s, u, cur, to, W::get(s.w, e));
       }
   }
-  flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
 // ------------------------------------------------------------------ hubs
@@ -993,11 +997,13 @@ __global__ void __launch_bounds__(HUB_NT) k_hub_build(ScanCtx s) {
 template <bool LOUV, bool NK>
 __device__ __forceinline__ void hub_decide(const ScanCtx& s, int32_t h, int32_t v, int32_t cur,
                                            typename KeyOf<LOUV, NK>::T fk, int32_t fc, bool hc, int64_t kc,
-                                           int64_t volv, int64_t& n_act, int64_t& n_arcs, int64_t& n_def) {
+                                           int64_t volv, int64_t& n_act, int64_t& n_arcs, int64_t& n_def,
+                                           int64_t& n_marcs) {
   const int32_t target = decide<LOUV, NK>(s, v, cur, fk, fc, hc, kc, volv);
   const int def = act_single(s, v, cur, target);
   n_def += def;
   if (target != cur && !def) {
+    n_marcs += s.off[v + 1] - s.off[v];
     s.hub_mv[3 * h] = 1;
     s.hub_mv[3 * h + 1] = cur;
     s.hub_mv[3 * h + 2] = target;
@@ -1018,7 +1024,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
   const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   const int64_t n = (int64_t)*s.small_cnt;
-  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
   for (int64_t q = warp; q < n; q += nwarps) {
     const int32_t h = s.small_list[q];
     const int32_t v = s.hub_list[h];
@@ -1064,9 +1070,9 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
     reduce_best(bk, bc, 32);
     const unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
-    if (lane == 0) hub_decide<LOUV, NK>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def);
+    if (lane == 0) hub_decide<LOUV, NK>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def, n_marcs);
   }
-  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
 // Every item scans HUB_SLICE histogram entries of one active hub; the last
@@ -1087,7 +1093,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       if (s.hub_item_first[h] == it) s.hub_rb[h] = 0;
     }
   }
-  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
   const int64_t n_ev = (int64_t)*s.ev_cnt;
   for (int64_t q = blockIdx.x; q < n_ev; q += gridDim.x) {
     const int64_t it = s.ev_list[q];
@@ -1168,14 +1174,14 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       }
       const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
       const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
-      hub_decide<LOUV, NK>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def);
+      hub_decide<LOUV, NK>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def, n_marcs);
       s.hub_done[h] = 0;
       s.hub_cur[h] = 0;
       s.hub_hascur[h] = 0;
     }
     __syncthreads();
   }
-  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def);
+  flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
 // ------------------------------------------------------------------ frontier
@@ -1691,10 +1697,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     CD_CHECK(cudaStreamSynchronize(st));
     const int64_t* h = g->h_ctr;
     const int64_t moves = h[C_MOVES], deferred = h[C_DEFERRED];
-    int64_t act = 0, arcs = 0;
+    int64_t act = 0, arcs = 0, cands = 0;
     for (int b = 0; b < NBINS; ++b) {
       act += h[C_BIN0 + 3 * b];
       arcs += h[C_BIN0 + 3 * b + 1];
+      cands += h[C_BIN0 + 3 * b + 2];
     }
     for (auto& mk : marks) {
       const int b = mk.second;
@@ -1744,6 +1751,8 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     tr.arcs = arcs;
     tr.moved = moves;
     tr.deferred = deferred;
+    tr.cands = cands;
+    tr.moved_arcs = h[C_MARCS];
     tr.scan_ms = tr.round_ms = 0.f;
     if (g->timing) {
       cudaEventRecord(ev[2], st);

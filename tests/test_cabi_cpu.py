@@ -4,6 +4,7 @@ the ctypes structures match the header's layout."""
 import ctypes
 import os
 import re
+import shutil
 import subprocess
 
 import pytest
@@ -48,11 +49,29 @@ def test_status_strings_and_defaults_without_gpu():
     assert cd.cd_status_string(12345) == "unknown status"
 
 
-def test_struct_layouts_match_header():
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    the C compiler gives the header's struct."""
     import paper_2507_06471_gb300 as cd
-    assert ctypes.sizeof(cd.cd_params) == 48
-    assert ctypes.sizeof(cd.cd_round_trace) == 48
-    assert ctypes.sizeof(cd.cd_kernel_profile) == 56
+    structs = [cd.cd_params, cd.cd_round_trace, cd.cd_kernel_profile, cd.cd_request_result]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cdgpu.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'  printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    (tmp_path / "layout.c").write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe),
+                           str(tmp_path / "layout.c")])
+    got = dict(ln.split() for ln in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
 
 
 def test_oracle_and_generator_build_on_host():

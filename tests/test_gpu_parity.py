@@ -99,6 +99,8 @@ def same_trace(gpu_trace, otr, level=0):
     assert [t["deferred"] for t in rows] == otr.deferred.tolist()
     assert [t["active"] for t in rows] == otr.active.tolist()
     assert [t["arcs"] for t in rows] == otr.arcs.tolist()
+    assert [t["cands"] for t in rows] == otr.cands.tolist()
+    assert [t["moved_arcs"] for t in rows] == otr.moved_arcs.tolist()
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))

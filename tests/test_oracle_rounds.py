@@ -10,7 +10,10 @@ fix is the schedule around them, under the readings the oracle states:
   defers;
 - the next round examines the moved vertices, their neighbours and the
   deferred vertices; LPA stops after a round with moved + deferred <= 0,
-  local moving after a round with no move and no deferral.
+  local moving after a round with no move and no deferral;
+- the trace counts, per round, the examined vertices, their arcs, their
+  distinct neighbour labels (candidate pairs, the own label included) and
+  the arcs of the vertices that moved.
 
 The coin values are literals below, checked against the SplitMix64 stream the
 published reference vector pins (tests/golden); with sched_seed = 1234567 the
@@ -73,19 +76,22 @@ LPA_CASES = {
     # coins 1,1: they swap to [1,0]. r2: coins 1,1: swap back to [0,1].
     # r3: 0 defers (coin 0), 1 commits to 0. r4: nobody wants to move.
     "k2": (K2, [[0, 1], [1, 0], [0, 1], [0, 0], [0, 0]],
-           dict(moved=[0, 2, 2, 1, 0], deferred=[2, 0, 0, 1, 0], active=[2, 2, 2, 2, 2], arcs=[2] * 5)),
+           dict(moved=[0, 2, 2, 1, 0], deferred=[2, 0, 0, 1, 0], active=[2, 2, 2, 2, 2], arcs=[2] * 5,
+                cands=[2] * 5, moved_arcs=[0, 2, 2, 1, 0])),
     # r0: wants 0->1, 1->0, 2->1, 3->4, 4->2 (ties to the smallest label);
     #     coins commit 2 and 4: [0,1,1,3,2].
     # r1: 1, 2 keep (their label attains the maximum); 0->1, 3->2, 4->1;
     #     coins commit 0 and 3, 4 defers: [1,1,1,2,2].
     # r2: examines {0,3} + neighbours {1,4} + deferred {4}: nobody moves.
     "path": (PATH, [[0, 1, 1, 3, 2], [1, 1, 1, 2, 2], [1, 1, 1, 2, 2]],
-             dict(moved=[2, 2, 0], deferred=[3, 1, 0], active=[5, 5, 4], arcs=[8, 8, 6])),
+             dict(moved=[2, 2, 0], deferred=[3, 1, 0], active=[5, 5, 4], arcs=[8, 8, 6],
+                  cands=[8, 8, 5], moved_arcs=[4, 2, 0])),
     # r0: centre wants 1, leaves want 0; coins commit 2 and 4: [0,1,0,3,0].
     # r1: centre keeps 0 (weight 2), leaves 1 and 3 commit to 0.
     # r2: examines {1,3} + centre: nobody moves.
     "star": (STAR, [[0, 1, 0, 3, 0], [0, 0, 0, 0, 0], [0, 0, 0, 0, 0]],
-             dict(moved=[2, 2, 0], deferred=[3, 0, 0], active=[5, 5, 3], arcs=[8, 8, 6])),
+             dict(moved=[2, 2, 0], deferred=[3, 0, 0], active=[5, 5, 3], arcs=[8, 8, 6],
+                  cands=[8, 7, 3], moved_arcs=[2, 2, 0])),
 }
 
 
@@ -110,7 +116,8 @@ LM_CASES = {
     # r1 examines only the deferred vertex 1; coin 1: it joins 0.
     # r2 examines 1 and its neighbour 0: nothing left to gain.
     "k2": (K2, [[0, 1], [0, 0], [0, 0]],
-           dict(moved=[0, 1, 0], deferred=[1, 0, 0], active=[2, 1, 2], arcs=[2, 1, 2]), 1),
+           dict(moved=[0, 1, 0], deferred=[1, 0, 0], active=[2, 1, 2], arcs=[2, 1, 2],
+                cands=[2, 1, 2], moved_arcs=[0, 1, 0]), 1),
     # vol = 12, deg = (2,2,4,2,2).
     # r0: 0 -> 1 (G 8) and 3 -> 4 (G 8) are barred by the singleton rule;
     #     1 -> 0 (G 8), 2 -> 0 (G 4, ties to the smallest id), 4 -> 3 (G 8);
@@ -122,7 +129,8 @@ LM_CASES = {
     #     barred; 2 stays (G -4): [0,0,3,3,3].
     # r3 examines 0 and its neighbours 1, 2: no positive gain (2 -> 0 has G = 0).
     "bowtie": (BOWTIE, [[0, 1, 0, 3, 3], [1, 0, 3, 3, 3], [0, 0, 3, 3, 3], [0, 0, 3, 3, 3]],
-               dict(moved=[2, 3, 1, 0], deferred=[1, 0, 0, 0], active=[5, 5, 5, 3], arcs=[12, 12, 12, 8]), 6),
+               dict(moved=[2, 3, 1, 0], deferred=[1, 0, 0, 0], active=[5, 5, 5, 3], arcs=[12, 12, 12, 8],
+                    cands=[12, 10, 9, 6], moved_arcs=[6, 8, 2, 0]), 6),
 }
 
 
