@@ -122,9 +122,10 @@ struct cd_graph {
   int32_t* hub_blist = nullptr;            // hub_items: build items queued this round
   int32_t* hub_mlist = nullptr;            // hub_items: mark items queued this round
   unsigned long long* hub_lcnt = nullptr;  // 2: queued build and mark items
-  int32_t* hub_cl = nullptr;               // 4 x nhubs: hubs rebuilt by clusters of 1, 2, 4, 8 CTAs
-  unsigned long long* hub_ccnt = nullptr;  // 4: their counts
+  int32_t* hub_cl = nullptr;               // 5 x nhubs: hubs rebuilt per build class
+  unsigned long long* hub_ccnt = nullptr;  // 5: their counts
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
+  bool cols_distinct = false;      // no row repeats a column (strictly increasing input rows, or coarse rows)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
   int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads (512 above 1024); above: hub
 
@@ -211,6 +212,7 @@ struct RunOpts {
   uint64_t sched_seed;
   int32_t level;
   int async_mode = 0;  // committed moves take effect at once (the coin still defers half of them)
+  bool singleton_start = false;  // the run starts from C[v] = v (Sigma_tot = deg_w, sizes 1)
 };
 // Algorithm 1 / Algorithm 2 round loops on g->C (device). Louvain: g->C holds
 // the initial partition; sigma/csize are rebuilt from it.

@@ -104,7 +104,7 @@ int profile_flush(cd_graph* g) {
 namespace {
 
 constexpr int NT = 256;
-constexpr int NSTATS = 4 + NBINS;
+constexpr int NSTATS = 5 + NBINS;
 
 __device__ __forceinline__ void fail(int32_t* status, int code) { atomicCAS(status, 0, code); }
 
@@ -146,62 +146,158 @@ __global__ void k_offsets_check(const OffT* __restrict__ in, int64_t n, int64_t 
   }
 }
 
-// Warp per vertex: bounds-check columns and weights, deg_w with loops twice,
-// loop count, vol(V), per-bin vertex counts. stats: [0] vol, [1] loops,
-// [2] isolated, [3] largest deg_w, [4..4+NBINS) bin counts.
+// Ingest: bounds-check columns and weights, deg_w with loops twice, loop
+// count, vol(V), per-bin vertex counts, and whether every row's columns are
+// strictly increasing (then no row repeats a column). stats: [0] vol,
+// [1] loops, [2] isolated, [3] largest deg_w, [4..4+NBINS) bin counts,
+// [4+NBINS] rows not strictly increasing.
+//
+// Load balance: each lane owns one vertex of its warp's 32 consecutive ones
+// and sums a row of at most INGEST_LANE arcs alone; the warp sums the rows of
+// up to INGEST_WARP arcs one at a time with coalesced loads; longer rows are
+// listed for k_ingest_big (a CTA per row).
+constexpr int INGEST_LANE = 32;
+constexpr int INGEST_WARP = 4096;
+constexpr int ST_UNSORTED = 4 + NBINS;
+
+struct RowSum {
+  long long s, loops;
+  bool unsorted;
+};
+
+template <class W>
+__device__ __forceinline__ void ingest_arc(const int32_t* __restrict__ cols, const void* w, int64_t n, int64_t v,
+                                           int64_t e, int64_t beg, int loops_twice, RowSum& r, int32_t* status) {
+  const int32_t u = cols[e];
+  const int64_t x = W::get(w, e);
+  if (u < 0 || u >= n) fail(status, CD_EBOUNDS);
+  if (x < 1) fail(status, CD_EINVAL);
+  r.s += x;
+  if (u == v) {
+    if (loops_twice) r.s += x;  // input convention: the loop arc carries L
+    ++r.loops;
+  }
+  if (e > beg && cols[e - 1] >= u) r.unsorted = true;
+}
+
+__device__ __forceinline__ void ingest_stats(unsigned long long* sb, int64_t d, long long s) {
+  atomicMax(&sb[3], (unsigned long long)s);
+  if (d == 0)
+    atomicAdd(&sb[2], 1ull);
+  else
+    atomicAdd(&sb[4 + bin_of(d)], 1ull);
+}
+
 template <class W>
 __global__ void __launch_bounds__(NT) k_ingest(const int64_t* __restrict__ off,
                                                const int32_t* __restrict__ cols, const void* w,
                                                int64_t n, int loops_twice, int64_t* __restrict__ degw,
-                                               unsigned long long* stats, int32_t* status) {
+                                               unsigned long long* stats, int32_t* status,
+                                               int32_t* big, unsigned long long* nbig) {
   __shared__ unsigned long long sb[NSTATS];
-  if (threadIdx.x < NSTATS) sb[threadIdx.x] = 0;
+  for (int i = threadIdx.x; i < NSTATS; i += NT) sb[i] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t warp = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * NT) >> 5;
   unsigned long long my_vol = 0, my_loops = 0;
-  for (int64_t v = warp; v < n; v += nwarps) {
-    int64_t beg = off[v], end = off[v + 1];
-    int64_t s = 0, loops = 0;
-    for (int64_t e = beg + lane; e < end; e += 32) {
-      int32_t u = cols[e];
-      int64_t x = W::get(w, e);
-      if (u < 0 || u >= n) fail(status, CD_EBOUNDS);
-      if (x < 1) fail(status, CD_EINVAL);
-      s += x;
-      if (u == v) {
-        if (loops_twice) s += x;  // input convention: the loop arc carries L
-        ++loops;
+  bool my_unsorted = false;
+  for (int64_t v0 = warp * 32; v0 < n; v0 += nwarps * 32) {  // whole warps iterate together
+    const int64_t v = v0 + lane;
+    const bool ok = v < n;
+    const int64_t beg = ok ? off[v] : 0, end = ok ? off[v + 1] : 0;
+    const int64_t d = end - beg;
+    RowSum r{0, 0, false};
+    if (d <= INGEST_LANE) {
+      for (int64_t e = beg; e < end; ++e) ingest_arc<W>(cols, w, n, v, e, beg, loops_twice, r, status);
+      if (ok) {
+        degw[v] = r.s;
+        my_vol += (unsigned long long)r.s;
+        my_loops += (unsigned long long)r.loops;
+        my_unsorted |= r.unsorted;
+        ingest_stats(sb, d, r.s);
+      }
+    } else if (d > INGEST_WARP) {
+      big[atomicAdd(nbig, 1ull)] = (int32_t)v;
+    }
+    unsigned todo = __ballot_sync(FULL, d > INGEST_LANE && d <= INGEST_WARP);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t vv = v0 + src;
+      const int64_t b = __shfl_sync(FULL, beg, src), en = __shfl_sync(FULL, end, src);
+      RowSum q{0, 0, false};
+      for (int64_t e = b + lane; e < en; e += 32) ingest_arc<W>(cols, w, n, vv, e, b, loops_twice, q, status);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        q.s += __shfl_xor_sync(FULL, q.s, o);
+        q.loops += __shfl_xor_sync(FULL, q.loops, o);
+      }
+      my_unsorted |= q.unsorted;
+      if (lane == src) {
+        degw[vv] = q.s;
+        my_vol += (unsigned long long)q.s;
+        my_loops += (unsigned long long)q.loops;
+        ingest_stats(sb, en - b, q.s);
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(FULL, s, o);
-      loops += __shfl_xor_sync(FULL, loops, o);
-    }
-    if (lane == 0) {
-      degw[v] = s;
-      my_vol += (unsigned long long)s;
-      my_loops += (unsigned long long)loops;
-      int64_t d = end - beg;
-      atomicMax(&sb[3], (unsigned long long)s);
-      if (d == 0)
-        atomicAdd(&sb[2], 1ull);
-      else
-        atomicAdd(&sb[4 + bin_of(d)], 1ull);
-    }
   }
-  if (lane == 0) {
-    atomicAdd(&sb[0], my_vol);
-    atomicAdd(&sb[1], my_loops);
-  }
+  atomicAdd(&sb[0], my_vol);
+  atomicAdd(&sb[1], my_loops);
+  if (my_unsorted) sb[ST_UNSORTED] = 1;
   __syncthreads();
   if (threadIdx.x < NSTATS && sb[threadIdx.x]) {
     if (threadIdx.x == 3)
       atomicMax(&stats[3], sb[3]);
     else
       atomicAdd(&stats[threadIdx.x], sb[threadIdx.x]);
+  }
+}
+
+// The rows k_ingest listed (more than INGEST_WARP arcs): a CTA per row.
+template <class W>
+__global__ void __launch_bounds__(NT) k_ingest_big(const int64_t* __restrict__ off,
+                                                   const int32_t* __restrict__ cols, const void* w,
+                                                   int64_t n, int loops_twice, int64_t* __restrict__ degw,
+                                                   unsigned long long* stats, int32_t* status,
+                                                   const int32_t* __restrict__ big,
+                                                   const unsigned long long* __restrict__ nbig) {
+  __shared__ long long red[2][NT / 32];
+  __shared__ int uns;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nb = (int64_t)*nbig;
+  for (int64_t q = blockIdx.x; q < nb; q += gridDim.x) {
+    const int64_t v = big[q];
+    const int64_t beg = off[v], end = off[v + 1];
+    if (threadIdx.x == 0) uns = 0;
+    RowSum r{0, 0, false};
+    for (int64_t e = beg + threadIdx.x; e < end; e += NT) ingest_arc<W>(cols, w, n, v, e, beg, loops_twice, r, status);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      r.s += __shfl_xor_sync(FULL, r.s, o);
+      r.loops += __shfl_xor_sync(FULL, r.loops, o);
+    }
+    if (lane == 0) {
+      red[0][wid] = r.s;
+      red[1][wid] = r.loops;
+    }
+    __syncthreads();
+    if (r.unsorted) uns = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long s = 0, loops = 0;
+      for (int i = 0; i < NT / 32; ++i) {
+        s += red[0][i];
+        loops += red[1][i];
+      }
+      degw[v] = s;
+      atomicAdd(&stats[0], (unsigned long long)s);
+      if (loops) atomicAdd(&stats[1], (unsigned long long)loops);
+      atomicMax(&stats[3], (unsigned long long)s);
+      atomicAdd(&stats[4 + bin_of(end - beg)], 1ull);
+      if (uns) atomicOr(&stats[ST_UNSORTED], 1ull);
+    }
+    __syncthreads();
   }
 }
 
@@ -285,6 +381,11 @@ __global__ void k_labels_check(const int32_t* __restrict__ lab, int64_t n, int32
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     if (lab[i] < 0 || lab[i] >= n) fail(status, CD_EINVAL);
+}
+
+unsigned grid_cap_u(int64_t blocks, int64_t cap) {
+  if (blocks < 1) blocks = 1;
+  return (unsigned)(blocks < cap ? blocks : cap);
 }
 
 unsigned grid_for(int64_t work, int per_block = NT) {
@@ -373,6 +474,7 @@ int build_bins(cd_graph* g);
 // Scalars, bins and hub structures of a graph whose CSR, weights and deg_w
 // are in place; stats from k_ingest.
 int finish_graph(cd_graph* g, const unsigned long long* stats) {
+  g->cols_distinct = stats[ST_UNSORTED] == 0;  // strictly increasing rows; aggregation sets it for coarse rows
   g->vol = (int64_t)stats[0];
   g->n_isolated = (int64_t)stats[2];
   g->max_degw = (int64_t)stats[3];
@@ -477,8 +579,8 @@ int build_bins(cd_graph* g) {
     if ((rc = dev_alloc_t(&g->hub_rb, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_flist, 2 * nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_fcnt, 2, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_cl, 4 * nh, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_ccnt, 4, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_cl, 5 * nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_ccnt, 5, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_used, nh, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_item_first, nh + 1, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_blist, g->hub_items, s))) return rc;
@@ -495,7 +597,7 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaMemsetAsync(g->hub_used, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_fcnt, 0, 2 * 8, s));
-    CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, 4 * 8, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, 5 * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
@@ -524,22 +626,38 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
   int rc = dev_alloc_t(&d_stats, NSTATS, s);
   if (rc) return rc;
   CD_CHECK(cudaMemsetAsync(d_stats, 0, (NSTATS) * sizeof(unsigned long long), s));
+  int32_t* big = nullptr;
+  unsigned long long* nbig = nullptr;
+  const int64_t big_cap = g->nnz / (INGEST_WARP + 1) + 1;  // rows longer than INGEST_WARP arcs, at most
+  if ((rc = dev_alloc_t(&big, big_cap, s)) || (rc = dev_alloc_t(&nbig, 1, s))) {
+    dev_free(big, s);
+    dev_free(d_stats, s);
+    return rc;
+  }
+  CD_CHECK(cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s));
   {
     KTimer t(g, K_UPLOAD, (double)g->nnz * (4 + (g->wkind == W_I32 ? 4 : g->wkind == W_I64 ? 8 : 0)) +
                               (double)g->n * 16);
     if (g->n > 0) {
-      unsigned gr = grid_for(g->n * 32);
-      if (g->wkind == W_UNIT)
-        CD_LAUNCH(k_ingest<WUnit><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                         g->status));
-      else if (g->wkind == W_I32)
-        CD_LAUNCH(k_ingest<WI32><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                        g->status));
-      else
-        CD_LAUNCH(k_ingest<WI64><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,
-                                        g->status));
+      const unsigned gr = grid_for((g->n + 31) / 32 * 32);
+      const unsigned gb = grid_cap_u(big_cap, 152 * 8);
+#define CD_INGEST(WT)                                                                                      \
+  CD_LAUNCH(k_ingest<WT><<<gr, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats,     \
+                                           g->status, big, nbig));                                         \
+  CD_LAUNCH(k_ingest_big<WT><<<gb, NT, 0, s>>>(g->off, g->cols, g->w, g->n, loops_twice, g->degw, d_stats, \
+                                               g->status, big, nbig))
+      if (g->wkind == W_UNIT) {
+        CD_INGEST(WUnit);
+      } else if (g->wkind == W_I32) {
+        CD_INGEST(WI32);
+      } else {
+        CD_INGEST(WI64);
+      }
+#undef CD_INGEST
     }
   }
+  dev_free(big, s);
+  dev_free(nbig, s);
   CD_CHECK(cudaGetLastError());
   CD_CHECK(cudaMemcpyAsync(stats_host, d_stats, (NSTATS) * sizeof(unsigned long long),
                            cudaMemcpyDeviceToHost, s));

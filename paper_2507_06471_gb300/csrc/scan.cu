@@ -138,8 +138,8 @@ struct ScanCtx {
   int32_t* hub_blist;                // build items of the hubs being rebuilt this round
   int32_t* hub_mlist;                // mark items of the hubs that moved this round
   unsigned long long* hub_lcnt;      // [0] build items, [1] mark items
-  int32_t* hub_cl;                   // 4 x nhubs: hubs rebuilt by clusters of 1, 2, 4, 8 CTAs
-  unsigned long long* hub_ccnt;      // 4: their counts
+  int32_t* hub_cl;                   // 5 x nhubs: hubs rebuilt per build class (one CTA small/large, clusters of 2, 4, 8)
+  unsigned long long* hub_ccnt;      // 5: their counts
   const int32_t* ev_list;            // evaluate items (of large hubs) to run this round
   const unsigned long long* ev_cnt;  // their number
   const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
@@ -753,9 +753,21 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
 // therefore reads its distinct labels instead of its whole row.
 
 constexpr int HUB_CL_SLOTS = 12288;    // table slots per CTA of a cluster build (96 KB: 2 CTAs per SM)
-constexpr int HUB_CL1_SLOTS = 8192;    // a one-CTA build (64 KB: 3 CTAs per SM)
-__host__ __device__ constexpr int hub_cl_slots(int c) { return c == 1 ? HUB_CL1_SLOTS : HUB_CL_SLOTS; }
-__host__ __device__ constexpr size_t hub_cl_smem(int c) { return (size_t)hub_cl_slots(c) * 8; }
+constexpr int HUB_CL1_SLOTS = 8192;    // a one-CTA build of 512 threads (64 KB: 3 CTAs per SM)
+constexpr int HUB_CL0_SLOTS = 4096;    // a one-CTA build of 256 threads (32 KB: 7 CTAs per SM)
+constexpr int HUB_NCLASS = 5;          // build classes: one CTA (small, large), clusters of 2, 4, 8
+// Build class of a hub table of `cap` packed slots: 0..4, or -1 (too large: chunked global inserts).
+__host__ __device__ constexpr int hub_class(int64_t cap) {
+  return cap <= HUB_CL0_SLOTS ? 0 : cap <= HUB_CL1_SLOTS ? 1 : cap <= 2 * HUB_CL_SLOTS ? 2
+       : cap <= 4 * HUB_CL_SLOTS ? 3 : cap <= 8 * HUB_CL_SLOTS ? 4 : -1;
+}
+template <int CI> struct HubClass;  // CTAs per cluster, threads per CTA, table slots per CTA
+template <> struct HubClass<0> { static constexpr int C = 1, NT = 256, SLOTS = HUB_CL0_SLOTS; };
+template <> struct HubClass<1> { static constexpr int C = 1, NT = 512, SLOTS = HUB_CL1_SLOTS; };
+template <> struct HubClass<2> { static constexpr int C = 2, NT = 512, SLOTS = HUB_CL_SLOTS; };
+template <> struct HubClass<3> { static constexpr int C = 4, NT = 512, SLOTS = HUB_CL_SLOTS; };
+template <> struct HubClass<4> { static constexpr int C = 8, NT = 512, SLOTS = HUB_CL_SLOTS; };
+template <int CI> constexpr size_t hub_cl_smem() { return (size_t)HubClass<CI>::SLOTS * 8; }
 constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
 constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
 
@@ -799,9 +811,9 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       __syncthreads();
       continue;
     }
-    if (!s.hub_wide && cap <= 8 * HUB_CL_SLOTS) {  // a cluster builds it and writes the whole table
+    if (!s.hub_wide && hub_class(cap) >= 0) {  // one CTA or a cluster builds it and writes the whole table
       if (threadIdx.x == 0) {
-        const int c = cap <= HUB_CL1_SLOTS ? 0 : cap <= 2 * HUB_CL_SLOTS ? 1 : cap <= 4 * HUB_CL_SLOTS ? 2 : 3;
+        const int c = hub_class(cap);
         s.hub_used[h] = 0;
         s.hub_rb[h] = HUB_REBUILD;  // cleared by the cluster once built
         s.hub_cl[(int64_t)c * s.nhubs + (int64_t)atomicAdd(&s.hub_ccnt[c], 1ull)] = h;
@@ -836,41 +848,87 @@ constexpr int HUB_NT = 512;
 // A hub table of at most C x hub_cl_slots(C) packed slots is rebuilt from the
 // hub's row by a cluster of C CTAs: the table is laid out in its final hash
 // order across the cluster's shared memories (CTA p holds slots
-// [p S, (p+1) S)), every arc's label is added there with shared-memory
-// atomics (remote ones through distributed shared memory), and each CTA then
-// writes its part with coalesced stores. No global atomics.
-template <class W, int C>
-__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_cl(ScanCtx s) {
-  extern __shared__ __align__(16) unsigned long long T[];  // hub_cl_slots(C)
-  __shared__ unsigned long long st_w[HUB_NT / 32][32];
+// [p S, (p+1) S)), every arc's label is added there (remote slots through
+// distributed shared memory), and each CTA then writes its part with
+// coalesced stores. No global atomics. In shared memory a slot is two 32-bit
+// words, the label and its count (packed tables have every count < 2^32), so
+// a probe past an occupied slot is a plain 32-bit load, only an empty slot is
+// claimed with a compare-and-swap, and the count takes a 32-bit add.
+template <int C>
+__device__ __forceinline__ bool hub_cl_insert(cg::cluster_group& cl, int32_t* K, uint32_t* V, int64_t cap,
+                                              int64_t S, int32_t lbl, uint32_t sum) {
+  const uint32_t home = (uint32_t)hub_home(lbl, cap);
+  if constexpr (C == 1) {  // the whole table is local
+    uint32_t slot = home;
+    for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
+      int32_t k = *(volatile int32_t*)&K[slot];
+      if (k == EMPTY) k = atomicCAS(&K[slot], EMPTY, lbl);
+      if (k == EMPTY || k == lbl) {
+        atomicAdd(&V[slot], sum);
+        return k == EMPTY;
+      }
+      slot = slot + 1 == (uint32_t)cap ? 0 : slot + 1;
+    }
+  } else {
+    // slot = owner * S + local (tables here are < 2^32 slots); probing steps
+    // local and carries into the next owner, wrapping at cap
+    uint32_t owner = home / (uint32_t)S, local = home - owner * (uint32_t)S;
+    for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
+      int32_t* pk = cl.map_shared_rank(K + local, owner);
+      int32_t k = *(volatile int32_t*)pk;
+      if (k == EMPTY) k = atomicCAS(pk, EMPTY, lbl);
+      if (k == EMPTY || k == lbl) {
+        atomicAdd(cl.map_shared_rank(V + local, owner), sum);
+        return k == EMPTY;
+      }
+      if (++local == (uint32_t)S || (int64_t)owner * S + local == cap) {
+        local = 0;
+        owner = (int64_t)(owner + 1) * S >= cap ? 0 : owner + 1;
+      }
+    }
+  }
+  return false;
+}
+
+template <class W, int CI>
+__global__ void __cluster_dims__(HubClass<CI>::C, 1, 1) __launch_bounds__(HubClass<CI>::NT)
+    k_hub_build_cl(ScanCtx s) {
+  constexpr int C = HubClass<CI>::C, NTB = HubClass<CI>::NT, SLOTS = HubClass<CI>::SLOTS;
+  extern __shared__ __align__(16) unsigned char hsm[];  // SLOTS keys, then as many counts
+  int32_t* K = (int32_t*)hsm;
+  uint32_t* V = (uint32_t*)(hsm + (size_t)SLOTS * 4);
+  __shared__ uint32_t st_w[NTB / 32][32];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int ci = C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3;
-  const int64_t n = (int64_t)*(volatile unsigned long long*)&s.hub_ccnt[ci];
-  const int32_t* list = s.hub_cl + (int64_t)ci * s.nhubs;
+  const int64_t n = (int64_t)*(volatile unsigned long long*)&s.hub_ccnt[CI];
+  const int32_t* list = s.hub_cl + (int64_t)CI * s.nhubs;
+  // the table starts clean; writing a hub's part out clears it again
+  for (int i = threadIdx.x; i < SLOTS; i += NTB) {
+    K[i] = EMPTY;
+    V[i] = 0;
+  }
+  if constexpr (C == 1) __syncthreads(); else cl.sync();
   for (int64_t q = blockIdx.x / C; q < n; q += gridDim.x / C) {  // uniform in the cluster
     const int32_t h = list[q];
     const int32_t v = s.hub_list[h];
     const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
     const int64_t S = (cap + C - 1) / C;  // slots per CTA
     const int64_t mine = cap - rank * S < S ? cap - rank * S : S;
-    for (int64_t i = threadIdx.x; i < S; i += HUB_NT) T[i] = SLOT_EMPTY;
-    if constexpr (C == 1) __syncthreads(); else cl.sync();  // every part is cleared before any insert
     const int64_t beg = s.off[v], end = s.off[v + 1];
     const int64_t share = (end - beg + C - 1) / C;
     const int64_t a0 = beg + rank * share, a1 = a0 + share < end ? a0 + share : end;
     int claimed = 0;
     constexpr int U = 4;  // arcs per thread per step: their loads and gathers are in flight together
-    for (int64_t e0 = a0; e0 < a1; e0 += (int64_t)U * HUB_NT) {  // whole CTAs iterate together
+    for (int64_t e0 = a0; e0 < a1; e0 += (int64_t)U * NTB) {  // whole CTAs iterate together
       int32_t nb[U], lbl[U];
-      unsigned long long w[U];
+      uint32_t w[U];
 #pragma unroll
       for (int j = 0; j < U; ++j) {
-        const int64_t e = e0 + (int64_t)j * HUB_NT + threadIdx.x;
+        const int64_t e = e0 + (int64_t)j * NTB + threadIdx.x;
         const bool has = e < a1;
         nb[j] = has ? s.cols[e] : v;
-        w[j] = (has && nb[j] != v) ? (unsigned long long)W::get(s.w, e) : 0ull;
+        w[j] = (has && nb[j] != v) ? (uint32_t)W::get(s.w, e) : 0u;
       }
 #pragma unroll
       for (int j = 0; j < U; ++j)  // labels are >= 0; a non-candidate gets a lane-unique negative key
@@ -879,58 +937,31 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
       for (int j = 0; j < U; ++j) {
         const bool cand = lbl[j] >= 0;
         const unsigned peers = __match_any_sync(FULL, lbl[j]);
-        st_w[wid][lane] = w[j];
-        __syncwarp();
-        if (cand && (__ffs(peers) - 1) == lane) {
-          unsigned long long sum = 0;
+        uint32_t sum;
+        if constexpr (W::unit) {
+          sum = (uint32_t)__popc(peers);
+        } else {
+          st_w[wid][lane] = w[j];
+          __syncwarp();
+          sum = 0;
           unsigned m = peers;
           while (m) {
             sum += st_w[wid][__ffs(m) - 1];
             m &= m - 1;
           }
-          const unsigned long long x = ((unsigned long long)(uint32_t)lbl[j] << 32) | sum;
-          // slot = owner * S + local (tables here are < 2^32 slots); probing steps local
-          // and carries into the next owner, wrapping at cap
-          const uint32_t home = (uint32_t)hub_home(lbl[j], cap);
-          if constexpr (C == 1) {  // the whole table is local
-            uint32_t slot = home;
-            for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
-              const unsigned long long prev = atomicCAS(&T[slot], SLOT_EMPTY, x);
-              if (prev == SLOT_EMPTY) {
-                ++claimed;
-                break;
-              }
-              if ((int32_t)(prev >> 32) == lbl[j]) {
-                atomicAdd(&T[slot], sum);
-                break;
-              }
-              slot = slot + 1 == (uint32_t)cap ? 0 : slot + 1;
-            }
-          } else {
-            uint32_t owner = home / (uint32_t)S, local = home - owner * (uint32_t)S;
-            for (int64_t probe = 0; probe < cap; ++probe) {  // at most 2/3 of the slots fill: always ends
-              unsigned long long* p = cl.map_shared_rank(T + local, owner);
-              const unsigned long long prev = atomicCAS(p, SLOT_EMPTY, x);
-              if (prev == SLOT_EMPTY) {
-                ++claimed;
-                break;
-              }
-              if ((int32_t)(prev >> 32) == lbl[j]) {
-                atomicAdd(p, sum);
-                break;
-              }
-              if (++local == (uint32_t)S || (int64_t)owner * S + local == cap) {
-                local = 0;
-                owner = (int64_t)(owner + 1) * S >= cap ? 0 : owner + 1;
-              }
-            }
-          }
+          __syncwarp();
         }
-        __syncwarp();
+        if (cand && (__ffs(peers) - 1) == lane && hub_cl_insert<C>(cl, K, V, cap, S, lbl[j], sum)) ++claimed;
       }
     }
     if constexpr (C == 1) __syncthreads(); else cl.sync();  // every insert is done
-    for (int64_t i = threadIdx.x; i < mine; i += HUB_NT) s.hub_slot[base + rank * S + i] = T[i];
+    for (int64_t i = threadIdx.x; i < mine; i += NTB) {
+      const int32_t k = K[i];
+      s.hub_slot[base + rank * S + i] =
+          k == EMPTY ? SLOT_EMPTY : (((unsigned long long)(uint32_t)k << 32) | (unsigned long long)V[i]);
+      K[i] = EMPTY;
+      V[i] = 0;
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) claimed += __shfl_xor_sync(FULL, claimed, o);
     if (lane == 0 && claimed) atomicAdd(&s.hub_used[h], claimed);
@@ -939,7 +970,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(HUB_NT) k_hub_build_
       atomicAdd(&s.ctr[C_HUB_BARCS], (unsigned long long)(end - beg));
       atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
     }
-    if constexpr (C == 1) __syncthreads(); else cl.sync();  // parts written before the next hub clears them
+    if constexpr (C == 1) __syncthreads(); else cl.sync();  // parts cleared before the next hub's inserts
   }
 }
 constexpr int HUB_CAP = 2 * HUB_CHUNK;
@@ -1184,6 +1215,104 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
+// ------------------------------------------------------------------ first round from rows
+//
+// Round 0 of a run or level that starts from singletons (C[v] = v, Sigma_tot
+// = deg_w, every size 1) on a graph whose rows never repeat a column: the
+// neighbour label u of arc (v, u) is u itself and k_{v,u} = w(v, u), so the
+// decision is an argmax over v's row (LPA: largest w, then smallest u;
+// Louvain: largest vol(V) w - deg_w(v) Sigma_tot[u], then smallest u) without
+// label gathers or tables. v's own label has weight 0 (loops are not
+// neighbours), so G of Eq. deltaQ equals the candidate key. PER threads work
+// on a vertex (a sub-warp tile, a warp, or the whole CTA); the decision, the
+// coin and the marking of a committed move's neighbours are those of the
+// general scan. No hub histogram is built or updated here: round 0 counts as
+// a heavy round, so every hub table is built at the start of round 1.
+constexpr int FIRST_MARK = 100;  // profile marks of first-round launches: FIRST_MARK + bin
+
+template <bool LOUV, class W, bool NK, int PER>
+__global__ void __launch_bounds__(NT) k_first_round(ScanCtx s, const int32_t* __restrict__ list,
+                                                    const unsigned long long* __restrict__ count_p, int bin) {
+  typedef typename KeyOf<LOUV, NK>::T K;
+  static_assert(PER == 4 || PER == 8 || PER == 16 || PER == 32 || PER == NT, "threads per vertex");
+  constexpr int TW = PER < 32 ? PER : 32;  // width of the in-warp reduction
+  constexpr int GPB = NT / PER;            // vertices per CTA and pass
+  __shared__ K red_k[NW];
+  __shared__ int32_t red_c[NW];
+  __shared__ int32_t moved_to[GPB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gid = threadIdx.x / PER, gl = threadIdx.x % PER;
+  const int64_t count = (int64_t)*count_p;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
+  // whole CTAs iterate together (the reductions need every lane)
+  for (int64_t base = (int64_t)blockIdx.x * GPB; base < count; base += (int64_t)gridDim.x * GPB) {
+    const int64_t i = base + gid;
+    const bool valid = i < count;
+    const int32_t v = valid ? list[i] : 0;
+    const bool act = valid && is_active(s, v);
+    int64_t beg = 0, end = 0, dv = 0, volv = 0;
+    if (act) {
+      beg = s.off[v];
+      end = s.off[v + 1];
+      if (LOUV) {
+        dv = s.degw[v];
+        volv = vol_of(s, v);
+      }
+    }
+    K bk = K(0);
+    int32_t bc = NOCAND;
+    for (int64_t e = beg + gl; e < end; e += PER) {
+      const int32_t u = s.cols[e];
+      if (u == v) continue;
+      const int64_t wt = W::get(s.w, e);
+      const K key = LOUV ? cand_key<LOUV, NK>(s, u, wt, dv, volv) : K(wt);
+      ++n_cand;
+      if (better(key, u, bk, bc)) {
+        bk = key;
+        bc = u;
+      }
+    }
+    reduce_best(bk, bc, TW);
+    if constexpr (PER == NT) {
+      if (lane == 0) {
+        red_k[wid] = bk;
+        red_c[wid] = bc;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int w2 = 1; w2 < NW; ++w2)
+          if (better(red_k[w2], red_c[w2], bk, bc)) {
+            bk = red_k[w2];
+            bc = red_c[w2];
+          }
+    }
+    if (gl == 0) {
+      bool moved = false;
+      if (act) {
+        const int32_t target = decide<LOUV, NK>(s, v, v, bk, bc, false, 0, volv);
+        const int def = act_single(s, v, v, target);
+        n_def += def;
+        ++n_act;
+        n_arcs += end - beg;
+        moved = target != v && !def;
+        if (moved) n_marcs += end - beg;
+      }
+      if constexpr (PER == NT) moved_to[0] = moved ? 1 : 0;
+      else if (!moved) end = beg;  // nothing to mark
+    }
+    if constexpr (PER == NT) {
+      __syncthreads();
+      if (!moved_to[0]) end = beg;
+      __syncthreads();
+    } else {
+      end = __shfl_sync(FULL, end, lane - gl);  // the tile leader's verdict
+    }
+    if (s.mark)  // the neighbours of a committed move are examined next round
+      for (int64_t e = beg + gl; e < end; e += PER) s.flag_nxt[s.cols[e]] = 1;
+  }
+  flush_counters(s, bin, n_act, n_arcs, n_cand, n_def, n_marcs);
+}
+
 // ------------------------------------------------------------------ frontier
 
 struct BinBounds {
@@ -1405,10 +1534,11 @@ int set_smem_attrs() {
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk1_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_prepare, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)HUB_PREP_SMEM));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(1)));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(2)));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(4)));
-  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem(8)));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem<0>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem<1>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem<2>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem<3>()));
+  CD_CHECK(cudaFuncSetAttribute(k_hub_build_cl<W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hub_cl_smem<4>()));
   CD_CHECK(cudaFuncSetAttribute(k_hub_build<W, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)hub_smem<V>()));
   done = true;
@@ -1422,6 +1552,41 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
   double b = (double)act * (8 + 4 + 1) + (double)arcs * (4 + 4 + wbytes);
   if (louv) b += (double)act * (8 + 8 + 8) + (double)cands * 8;
   return b;
+}
+
+// Launch the first round from rows over every bin.
+template <bool LOUV, class W, bool NK>
+int launch_first_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
+  cudaStream_t st = g->stream;
+  auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
+  auto lst = [&](int b) { return (const int32_t*)g->bin_list + g->bin_start[b]; };
+  auto dcnt = [&](int b) { return (const unsigned long long*)g->full_cnt + b; };
+  static const int kname[NBINS] = {K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP,
+                                   K_SCAN_BLK128, K_SCAN_BLK512, K_HUB_EVAL};
+  for (int b = NBINS - 1; b >= 0; --b) {
+    const int64_t c = cnt(b);
+    if (c == 0) continue;
+    {
+      KTimer t(g, kname[b]);
+      switch (b) {
+        case B_T4: CD_LAUNCH((k_first_round<LOUV, W, NK, 4><<<grid_cap((c + 63) / 64), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
+        case B_T8: CD_LAUNCH((k_first_round<LOUV, W, NK, 8><<<grid_cap((c + 31) / 32), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
+        case B_T16: CD_LAUNCH((k_first_round<LOUV, W, NK, 16><<<grid_cap((c + 15) / 16), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
+        case B_HUB:
+        case B_BLK4: CD_LAUNCH((k_first_round<LOUV, W, NK, NT><<<grid_cap(c), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
+        default: CD_LAUNCH((k_first_round<LOUV, W, NK, 32><<<grid_cap((c + NW - 1) / NW), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
+      }
+    }
+    if (g->timing) marks.push_back({g->pending.size() - 1, b + FIRST_MARK});  // first-round bytes
+  }
+  return CD_OK;
+}
+
+template <bool LOUV, bool NK>
+int dispatch_first(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
+  if (g->wkind == W_UNIT) return launch_first_round<LOUV, WUnit, NK>(g, s, marks);
+  if (g->wkind == W_I32) return launch_first_round<LOUV, WI32, NK>(g, s, marks);
+  return launch_first_round<LOUV, WI64, NK>(g, s, marks);
 }
 
 template <bool LOUV, class W, class V, bool NK>
@@ -1438,10 +1603,11 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
-      CD_LAUNCH((k_hub_build_cl<W, 1><<<456, HUB_NT, hub_cl_smem(1), st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, hub_cl_smem(2), st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, hub_cl_smem(4), st>>>(s)));
-      CD_LAUNCH((k_hub_build_cl<W, 8><<<304, HUB_NT, hub_cl_smem(8), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 0><<<152 * 6, 256, hub_cl_smem<0>(), st>>>(s)));  // 6 CTAs per SM (registers)
+      CD_LAUNCH((k_hub_build_cl<W, 1><<<456, HUB_NT, hub_cl_smem<1>(), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, hub_cl_smem<2>(), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 3><<<304, HUB_NT, hub_cl_smem<3>(), st>>>(s)));
+      CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, hub_cl_smem<4>(), st>>>(s)));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
@@ -1570,6 +1736,9 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     }
     CD_LAUNCH(k_sigma32_all<<<grid_cap((n + NT - 1) / NT), NT, 0, st>>>(g->sigma, n, g->sigma32));
   }
+  // round 0 from the rows when every vertex starts alone and no row repeats a
+  // column (the asynchronous mode keeps the general scan)
+  const bool first_rows = o.singleton_start && g->cols_distinct && !o.async_mode;
   int32_t rounds = 0;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (g->timing)
@@ -1582,7 +1751,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (g->nhubs > 0) {
       CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
-      CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, 4 * sizeof(unsigned long long), st));
+      CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
     }
     ScanCtx s;
@@ -1681,7 +1850,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     }
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
-    if (louv) {
+    if (r == 0 && first_rows) {
+      if (!louv) rc = dispatch_first<false, false>(g, s, marks);
+      else if (g->vol < ((int64_t)1 << 31)) rc = dispatch_first<true, true>(g, s, marks);
+      else rc = dispatch_first<true, false>(g, s, marks);
+    } else if (louv) {
       // Louvain candidate keys vol(V) k - deg_w(v) Sigma_tot need 128 bits in
       // general; when vol(V) < 2^31 each product is < 2^62 and they fit in 64
       if (g->vol < ((int64_t)1 << 31)) rc = dispatch_round<true, true>(g, s, lists, counts, marks, v32);
@@ -1708,7 +1881,11 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       const int64_t ab = b >= 0 ? h[C_BIN0 + 3 * b] : 0;
       const int64_t rb = h[C_BIN0 + 3 * B_HUB + 1], cb = b >= 0 ? h[C_BIN0 + 3 * b + 2] : 0;
       double bytes;
-      if (b == -1)  // hub table builds: the arcs they read, the slots they wrote
+      if (b >= FIRST_MARK) {  // first round from rows: no label gathers
+        const int fb = b - FIRST_MARK;
+        const int64_t fa = h[C_BIN0 + 3 * fb], farcs = h[C_BIN0 + 3 * fb + 1], fc = h[C_BIN0 + 3 * fb + 2];
+        bytes = (double)fa * (8 + 4 + 1) + (double)farcs * (4 + wbytes) + (louv ? (double)fa * 24 + (double)fc * 8 : 0.0);
+      } else if (b == -1)  // hub table builds: the arcs they read, the slots they wrote
         bytes = (double)h[C_HUB_BARCS] * (4 + 4 + wbytes) + (double)h[C_HUB_BSLOTS] * 8;
       else if (b == B_HUB)  // hub evaluate: the candidates of every active hub
         bytes = (double)cb * (12 + 12 + (louv ? 8 : 0)) + (double)ab * (8 + 4);
@@ -1803,7 +1980,9 @@ int run_lpa(cd_graph* g, const RunOpts& o, int32_t* rounds_out) {
     CD_LAUNCH(k_init_singletons<<<grid_cap((g->n + NT - 1) / NT), NT, 0, g->stream>>>(g->C, g->sigma, g->csize,
                                                                             g->degw, g->n, 0));
   CD_CHECK(cudaGetLastError());
-  return run_rounds(g, o, false, nullptr, rounds_out);
+  RunOpts os = o;
+  os.singleton_start = true;
+  return run_rounds(g, os, false, nullptr, rounds_out);
 }
 
 int run_lpa_batched(cd_graph* g, const RunOpts& o, std::vector<int32_t>& rounds) {
@@ -1815,6 +1994,7 @@ int run_lpa_batched(cd_graph* g, const RunOpts& o, std::vector<int32_t>& rounds)
   CD_CHECK(cudaGetLastError());
   RunOpts ob = o;
   ob.batched = true;
+  ob.singleton_start = true;
   return run_rounds(g, ob, false, nullptr, nullptr, &rounds);
 }
 
@@ -1835,7 +2015,9 @@ int run_local_move(cd_graph* g, const RunOpts& o, int init_given, int64_t* moves
     }
   }
   CD_CHECK(cudaGetLastError());
-  return run_rounds(g, o, true, moves_out, rounds_out);
+  RunOpts os = o;
+  os.singleton_start = !init_given;
+  return run_rounds(g, os, true, moves_out, rounds_out);
 }
 
 RunOpts opts_from(const cd_params* p, int32_t level) {
