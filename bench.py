@@ -817,18 +817,32 @@ def run_graph(args, rank, world, local):
 
     # the method's per-round figures: the first LPA round and the first
     # local-moving round of level 0 (every vertex examined), median over steps
-    lpa0 = [tr[0][0] for tr in traces if tr[0]]
-    lv0 = [tr[1][0] for tr in traces if tr[1]]
     rounds = {"bytes": "per round: arcs x (column 4 + neighbour label 4 + weight) + examined vertices x 17 "
                        "(offsets, label, label write, flag) + 4 x arcs of moved vertices + n flag clears; "
                        "Louvain adds 8 per candidate pair, 8 per examined vertex, 24 per move",
               "time": "CUDA events on the library stream from the round's first to its last kernel "
                       "(scan_ms: up to the end of the scan kernels)",
+              "round0": "every vertex starts alone, so round 0 decides from the rows (labels are the vertex "
+                        "ids: no label gathers, no hub tables); round 1 is the first round that reads labels "
+                        "and builds the hub tables",
               "peak": peak}
-    if lpa0:
-        rounds["lpa_round0"] = round_figures(lpa0, False, wbytes, n, peak)
-    if lv0:
-        rounds["louvain_level0_round0"] = round_figures(lv0, True, wbytes, n, peak)
+    for k in (0, 1):
+        lpa_k = [tr[0][k] for tr in traces if len(tr[0]) > k]
+        lv_k = [[t for t in tr[1] if t["level"] == 0][k] for tr in traces
+                if sum(1 for t in tr[1] if t["level"] == 0) > k]
+        if lpa_k:
+            rounds[f"lpa_round{k}"] = round_figures(lpa_k, False, wbytes, n, peak)
+        if lv_k:
+            rounds[f"louvain_level0_round{k}"] = round_figures(lv_k, True, wbytes, n, peak)
+    # every round of the last step: arcs scanned over round time, and bytes over round time
+    last_lpa, last_lv = traces[-1]
+    for name, rows, louv in (("lpa_all_rounds", last_lpa, False), ("louvain_all_rounds", last_lv, True)):
+        ms_all = sum(t["round_ms"] for t in rows)
+        if ms_all > 0:
+            b_all = sum(round_bytes(t, louv, wbytes, n if louv is False or t["level"] == 0 else 0) for t in rows)
+            rounds[name] = {"rounds": len(rows), "ms": ms_all, "arcs": sum(t["arcs"] for t in rows),
+                            "gteps": sum(t["arcs"] for t in rows) / (ms_all / 1e3) / 1e9,
+                            "GBps": b_all / (ms_all / 1e3) / 1e9, "frac": b_all / (ms_all / 1e3) / 1e9 / peak}
 
     line = {
         "metric": METRIC_GTEPS,

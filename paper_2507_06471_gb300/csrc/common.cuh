@@ -134,7 +134,7 @@ struct cd_graph {
   int64_t* sigma = nullptr;
   uint32_t* sigma32 = nullptr;  // 32-bit copy for the gathers (allocated on first use)
   int32_t* csize = nullptr;
-  uint8_t* flag[2] = {nullptr, nullptr};
+  uint32_t* flag[2] = {nullptr, nullptr};  // needCheck / tmpNeedCheck bitmaps (n bits each)
   int32_t* mv_v = nullptr;  // committed moves: vertex, new label, old label
   int32_t* mv_c = nullptr;
   int32_t* mv_a = nullptr;

@@ -685,8 +685,8 @@ int ensure_run_state(cd_graph* g) {
   if ((rc = dev_alloc_t(&g->C, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->sigma, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->csize, g->n, s))) return rc;
-  if ((rc = dev_alloc_t(&g->flag[0], g->n, s))) return rc;
-  if ((rc = dev_alloc_t(&g->flag[1], g->n, s))) return rc;
+  if ((rc = dev_alloc_t(&g->flag[0], (g->n + 31) / 32 + 1, s))) return rc;
+  if ((rc = dev_alloc_t(&g->flag[1], (g->n + 31) / 32 + 1, s))) return rc;
   if ((rc = dev_alloc_t(&g->mv_v, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->mv_c, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->mv_a, g->n, s))) return rc;

@@ -100,8 +100,8 @@ struct ScanCtx {
   const int64_t* sigma;
   const uint32_t* sigma32;  // 32-bit copy of sigma for the gathers (vol(V) < 2^31, synchronous), or null
   const int32_t* csize;
-  const uint8_t* flag_cur;
-  uint8_t* flag_nxt;
+  const uint32_t* flag_cur;  // bitmaps of n bits: examined this round / next round
+  uint32_t* flag_nxt;
   int all_active;
   int mark;  // maintain the next-round flags (frontier on)
   int32_t* mv_v;
@@ -158,6 +158,11 @@ struct ScanCtx {
   const uint8_t* gfrozen;
   unsigned long long* gcnt;
 };
+
+// Flag vertex u for the next round (a bit in an L2-resident bitmap).
+__device__ __forceinline__ void flag_next(const ScanCtx& s, int32_t u) {
+  atomicOr(&s.flag_nxt[u >> 5], 1u << (u & 31));
+}
 
 // vol(V) of the graph v belongs to, and v's id inside that graph (the coin
 // uses graph-local ids so that a batched run draws what a solo run draws).
@@ -239,7 +244,7 @@ __device__ __forceinline__ void apply_now(const ScanCtx& s, int32_t v, int32_t c
 // Returns 1 if the move was deferred.
 __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t cur, int32_t target) {
   if (target == cur) return 0;
-  if (s.mark) s.flag_nxt[v] = 1;
+  if (s.mark) flag_next(s, v);
   count_change(s, v);
   if (commit_coin(s.seed, s.level, s.round, local_id(s, v))) {
     unsigned long long pos = atomicAdd(&s.ctr[C_MOVES], 1ull);
@@ -273,7 +278,7 @@ __device__ __forceinline__ void flush_counters(const ScanCtx& s, int bin, int64_
 
 __device__ __forceinline__ bool is_active(const ScanCtx& s, int32_t v) {
   if (s.gfrozen && s.gfrozen[s.gid[v]]) return false;
-  return s.all_active || s.flag_cur[v];
+  return s.all_active || ((s.flag_cur[v >> 5] >> (v & 31)) & 1u);
 }
 
 // Group weight of the lanes in `peers` (equal labels): popcount for unit
@@ -477,8 +482,8 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
       }
     }
     if (s.mark) {
-      if (commit && has) s.flag_nxt[u] = 1;  // the neighbours of a moved vertex
-      if (want && sub == 0) s.flag_nxt[v] = 1;
+      if (commit && has) flag_next(s, u);  // the neighbours of a moved vertex
+      if (want && sub == 0) flag_next(s, v);
     }
     if (s.nhubs > 0 && commit && cand) hub_neighbour_moved(s, u, cur, target, wt);
     if (sub == 0 && act) {
@@ -738,11 +743,120 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
     if (to >= 0 && (s.mark || s.nhubs > 0))
       for (int64_t e = beg + gl; e < end; e += GROUP) {
         const int32_t u = s.cols[e];
-        if (s.mark) s.flag_nxt[u] = 1;
+        if (s.mark) flag_next(s, u);
         if (s.nhubs > 0 && u != v) hub_neighbour_moved(s, u, cur, to, W::get(s.w, e));
       }
   }
   flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def, n_marcs);
+}
+
+// The warp bin (degrees 33..t_warp): a warp takes 32 listed vertices at a
+// time. Lane j loads vertex j's header; the warp then scans each active vertex
+// in turn (table inserts and evaluation as in k_scan_group) and lane j keeps
+// vertex j's best candidate. The 32 decisions, coins and move-list appends
+// then run in parallel, one lane per vertex, and the neighbours of the
+// committed moves are flagged (and their hub histograms updated) last.
+template <bool LOUV, class W, class V, bool NK>
+__global__ void __launch_bounds__(256, (LOUV || !W::unit) ? 4 : 5)
+    k_scan_warp(ScanCtx s, const int32_t* __restrict__ list, const unsigned long long* __restrict__ count_p) {
+  typedef typename KeyOf<LOUV, NK>::T K;
+  constexpr int CAP = WARP_CAP_SLOTS, WPB = 256 / 32;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int occ_n[WPB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  V* vals = (V*)smem + (size_t)wid * CAP;
+  int32_t* keys = (int32_t*)(smem + (size_t)WPB * CAP * sizeof(V)) + (size_t)wid * CAP;
+  int64_t* stage = (int64_t*)(smem + (size_t)WPB * CAP * (sizeof(V) + 4)) + wid * 32;
+  uint16_t* occ = (uint16_t*)(smem + (size_t)WPB * CAP * (sizeof(V) + 4) + (size_t)WPB * 32 * 8) + (size_t)wid * CAP;
+  for (int j = lane; j < CAP; j += 32) {
+    keys[j] = EMPTY;
+    vals[j] = 0;
+  }
+  if (lane == 0) occ_n[wid] = 0;
+  __syncwarp();
+  const int64_t count = (int64_t)*count_p;
+  const int64_t warp = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * 256) >> 5;
+  int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
+  for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    const int32_t my_v = i < count ? list[i] : 0;
+    const VHdr h = load_hdr<LOUV>(s, my_v, i < count);
+    K my_bk = K(0);
+    int32_t my_bc = NOCAND;
+    bool my_hc = false;
+    int64_t my_kc = 0;
+    for (unsigned am = __ballot_sync(FULL, h.act); am; am &= am - 1) {
+      const int j = __ffs(am) - 1;
+      const int32_t v = __shfl_sync(FULL, my_v, j);
+      const int64_t beg = __shfl_sync(FULL, h.beg, j), end = __shfl_sync(FULL, h.end, j);
+      const int32_t cur = __shfl_sync(FULL, h.cur, j);
+      const int64_t dv = LOUV ? __shfl_sync(FULL, h.dv, j) : 0;
+      const int64_t volv = LOUV ? __shfl_sync(FULL, h.vol, j) : 0;
+      const unsigned lg = 64 - __clzll((unsigned long long)(2 * (end - beg) - 1));  // 2^lg >= 2 deg
+      group_insert<W, V, 32>(s, v, beg, end, lane, keys, vals, occ, &occ_n[wid], lg, stage);
+      __syncwarp();
+      K bk = K(0);
+      int32_t bc = NOCAND;
+      bool hc = false;
+      int64_t kc = 0;
+      group_eval<LOUV, V, 32, NK>(s, cur, dv, volv, lane, keys, vals, occ, occ_n[wid], bk, bc, hc, kc, n_cand);
+      reduce_best(bk, bc, 32);
+      const unsigned hm = __ballot_sync(FULL, hc);
+      if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
+      if (lane == j) {
+        my_bk = bk;
+        my_bc = bc;
+        my_hc = hm != 0;
+        my_kc = kc;
+      }
+      __syncwarp();
+      if (lane == 0) occ_n[wid] = 0;
+      __syncwarp();
+    }
+    // the batch's decisions, one lane per vertex
+    int32_t target = h.cur;
+    if (h.act) target = decide<LOUV, NK>(s, my_v, h.cur, my_bk, my_bc, my_hc, my_kc, h.vol);
+    const bool want = h.act && target != h.cur;
+    const bool commit = want && commit_coin(s.seed, s.level, s.round, local_id(s, my_v));
+    if (want) count_change(s, my_v);
+    const unsigned cm = __ballot_sync(FULL, commit);
+    if (cm) {
+      const int first = __ffs(cm) - 1;
+      unsigned long long pos0 = 0;
+      if (lane == first) pos0 = atomicAdd(&s.ctr[C_MOVES], (unsigned long long)__popc(cm));
+      pos0 = __shfl_sync(FULL, pos0, first);
+      if (commit) {
+        const unsigned long long pos = pos0 + __popc(cm & ((1u << lane) - 1u));
+        s.mv_v[pos] = my_v;
+        s.mv_c[pos] = target;
+        s.mv_a[pos] = h.cur;
+        if (s.async_mode) apply_now(s, my_v, h.cur, target);
+      }
+    }
+    if (want && s.mark) flag_next(s, my_v);
+    if (h.act) {
+      ++n_act;
+      n_arcs += h.end - h.beg;
+      if (!commit && want) ++n_def;
+      if (commit) n_marcs += h.end - h.beg;
+    }
+    // committed moves: flag the neighbours for the next round and update the
+    // histograms of neighbouring hubs (their evaluation for this round is done)
+    if (s.mark || s.nhubs > 0)
+      for (unsigned m = cm; m; m &= m - 1) {
+        const int j = __ffs(m) - 1;
+        const int32_t v = __shfl_sync(FULL, my_v, j);
+        const int64_t beg = __shfl_sync(FULL, h.beg, j), end = __shfl_sync(FULL, h.end, j);
+        const int32_t from = __shfl_sync(FULL, h.cur, j), to = __shfl_sync(FULL, target, j);
+        for (int64_t e = beg + lane; e < end; e += 32) {
+          const int32_t u = s.cols[e];
+          if (s.mark) flag_next(s, u);
+          if (s.nhubs > 0 && u != v) hub_neighbour_moved(s, u, from, to, W::get(s.w, e));
+        }
+      }
+  }
+  flush_counters(s, B_WARP, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
 // ------------------------------------------------------------------ hubs
@@ -1308,7 +1422,7 @@ __global__ void __launch_bounds__(NT) k_first_round(ScanCtx s, const int32_t* __
       end = __shfl_sync(FULL, end, lane - gl);  // the tile leader's verdict
     }
     if (s.mark)  // the neighbours of a committed move are examined next round
-      for (int64_t e = beg + gl; e < end; e += PER) s.flag_nxt[s.cols[e]] = 1;
+      for (int64_t e = beg + gl; e < end; e += PER) flag_next(s, s.cols[e]);
   }
   flush_counters(s, bin, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
@@ -1429,7 +1543,7 @@ __global__ void __launch_bounds__(NT) k_hub_mark(ScanCtx s) {
     const int64_t end = a0 + HUB_CHUNK < rowend ? a0 + HUB_CHUNK : rowend;
     for (int64_t e = a0 + threadIdx.x; e < end; e += NT) {
       const int32_t u = s.cols[e];
-      if (s.mark) s.flag_nxt[u] = 1;
+      if (s.mark) flag_next(s, u);
       if (u == v) continue;
       hub_neighbour_moved(s, u, A, c, W::get(s.w, e));
     }
@@ -1527,7 +1641,7 @@ template <bool LOUV, class W, class V, bool NK>
 int set_smem_attrs() {
   static std::atomic<bool> done{false};  // idempotent; threads may race here
   if (done) return CD_OK;
-  CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true, NK>,
+  CD_CHECK(cudaFuncSetAttribute(k_scan_warp<LOUV, W, V, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)warp_smem<V>()));
   CD_CHECK(cudaFuncSetAttribute(k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false, NK>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blk4_smem<V>()));
@@ -1641,8 +1755,8 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP);
-      auto kern = k_scan_group<LOUV, W, V, 32, 256, WARP_CAP_SLOTS, B_WARP, true, NK>;
-      CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + NW - 1) / NW), 256, warp_smem<V>(),
+      auto kern = k_scan_warp<LOUV, W, V, NK>;
+      CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + 255) / 256), 256, warp_smem<V>(),
                         st>>>(s, lst(B_WARP), dcnt(B_WARP))));
     }
     if (g->timing) mark(B_WARP);
@@ -1721,9 +1835,10 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     CD_CHECK(cudaMemcpyAsync(g->hub_fcnt + 1, &nh, sizeof(nh), cudaMemcpyHostToDevice, st));
     CD_CHECK(cudaStreamSynchronize(st));  // nh lives on this stack frame
   }
-  uint8_t* fcur = g->flag[0];
-  uint8_t* fnxt = g->flag[1];
-  if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fcur, 1, n, st));
+  uint32_t* fcur = g->flag[0];
+  uint32_t* fnxt = g->flag[1];
+  const size_t fbytes = (size_t)((n + 31) / 32) * 4;  // bitmap words
+  if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fcur, 0xff, fbytes, st));
   const int wbytes = g->wkind == W_UNIT ? 0 : g->wkind == W_I32 ? 4 : 8;
   int64_t total_moves = 0;
   int64_t prev_moves = -1;
@@ -1747,7 +1862,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     if (g->timing) cudaEventRecord(ev[0], st);
     CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
     if (per_graph_stop) CD_CHECK(cudaMemsetAsync(g->gcnt, 0, g->nb * sizeof(int64_t), st));
-    if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, n, st));
+    if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, fbytes, st));
     if (g->nhubs > 0) {
       CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * g->nhubs * sizeof(int32_t), st));
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
