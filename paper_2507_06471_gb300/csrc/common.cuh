@@ -100,7 +100,7 @@ struct cd_graph {
   // otherwise two words (label, count).
   int64_t nhubs = 0, hub_slots = 0, hub_items = 0, hub_eval_items = 0;
   int hub_wide = 0;                        // 1: two-word slots
-  int32_t* hub_idx = nullptr;              // n: hub index of a vertex, -1 otherwise
+  uint32_t* hub_pref = nullptr;        // per 32-vertex word: hubs with smaller vertex ids (hub number = rank)
   uint32_t* hub_bits = nullptr;            // (n+31)/32: bit v set iff v is a hub
   int64_t* hub_tab = nullptr;              // nhubs+1
   unsigned long long* hub_slot = nullptr;  // hub_slots words (x2 when wide)

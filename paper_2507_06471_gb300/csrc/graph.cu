@@ -344,13 +344,26 @@ __global__ void __launch_bounds__(NT) k_bin_fill(const int64_t* __restrict__ off
   }
 }
 
-__global__ void k_hub_index(const int32_t* __restrict__ hubs, int64_t nh, int32_t* hub_idx,
-                            uint32_t* hub_bits) {
+__global__ void k_hub_bits(const int32_t* __restrict__ hubs, int64_t nh, uint32_t* hub_bits) {
   int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (h < nh) {
     const int32_t v = hubs[h];
-    hub_idx[v] = (int32_t)h;
     atomicOr(&hub_bits[v >> 5], 1u << (v & 31));
+  }
+}
+
+// Hubs are numbered in increasing vertex id, so the number of vertex u is its
+// rank among the hubs: hub_pref[u / 32] (hubs below 32 (u / 32)) plus the hub
+// bits below u in its word. hub_pref[w] = lower bound of 32 w in the sorted list.
+__global__ void k_hub_pref(const int32_t* __restrict__ hubs, int64_t nh, int64_t nwords, uint32_t* hub_pref) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += stride) {
+    int64_t lo = 0, hi = nh;  // first hub with vertex >= 32 w
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) / 2;
+      if ((int64_t)hubs[mid] < 32 * w) lo = mid + 1; else hi = mid;
+    }
+    hub_pref[w] = (uint32_t)lo;
   }
 }
 
@@ -408,7 +421,7 @@ void free_arrays(cd_graph* g) {
   void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
                 g->act_list,     g->act_cnt,       g->full_cnt,     g->act_ev,       g->act_small,
                 g->hub_big_items, g->hub_small,
-                g->hub_idx,      g->hub_bits,      g->hub_tab,       g->hub_slot,
+                g->hub_pref,      g->hub_bits,      g->hub_tab,       g->hub_slot,
                 g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
                 g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
@@ -426,7 +439,7 @@ void free_bins(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->bin_list,     g->act_list,    g->act_cnt,      g->full_cnt,  g->act_ev,
                 g->act_small,    g->hub_big_items, g->hub_small,
-                g->hub_idx,      g->hub_bits,     g->hub_tab,   g->hub_slot,
+                g->hub_pref,      g->hub_bits,     g->hub_tab,   g->hub_slot,
                 g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
                 g->hub_rb,       g->hub_used,     g->hub_item_first, g->hub_blist,
@@ -442,7 +455,7 @@ void free_bins(cd_graph* g) {
   g->hub_big_items = nullptr;
   g->hub_small = nullptr;
   g->n_small_hubs = g->n_big_items = 0;
-  g->hub_idx = nullptr;
+  g->hub_pref = nullptr;
   g->hub_bits = nullptr;
   g->hub_tab = nullptr;
   g->hub_slot = nullptr;
@@ -519,6 +532,15 @@ int build_bins(cd_graph* g) {
   int64_t nh = g->bin_start[B_HUB + 1] - g->bin_start[B_HUB];
   g->nhubs = nh;
   if (nh > 0) {
+    {  // hubs in increasing vertex id (their number is their rank)
+      std::vector<int32_t> hv(nh);
+      int32_t* dl = g->bin_list + g->bin_start[B_HUB];
+      CD_CHECK(cudaMemcpyAsync(hv.data(), dl, nh * 4, cudaMemcpyDeviceToHost, s));
+      CD_CHECK(cudaStreamSynchronize(s));
+      std::sort(hv.begin(), hv.end());
+      CD_CHECK(cudaMemcpyAsync(dl, hv.data(), nh * 4, cudaMemcpyHostToDevice, s));
+      CD_CHECK(cudaStreamSynchronize(s));  // hv dies here
+    }
     int64_t* d_rows = nullptr;
     if ((rc = dev_alloc_t(&d_rows, 2 * nh, s))) return rc;
     CD_LAUNCH(k_gather_rows<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->off, g->bin_list + g->bin_start[B_HUB],
@@ -561,7 +583,7 @@ int build_bins(cd_graph* g) {
       CD_CHECK(cudaMemcpyAsync(g->hub_small, small.data(), small.size() * 4, cudaMemcpyHostToDevice, s));
     if (!big_items.empty())
       CD_CHECK(cudaMemcpyAsync(g->hub_big_items, big_items.data(), big_items.size() * 4, cudaMemcpyHostToDevice, s));
-    if ((rc = dev_alloc_t(&g->hub_idx, g->n, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_pref, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_bits, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
     g->hub_wide = g->max_degw >= ((int64_t)1 << 32) ? 1 : 0;
@@ -601,10 +623,11 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaMemsetAsync(g->hub_cur, 0, nh * 8, s));
     CD_CHECK(cudaMemsetAsync(g->hub_hascur, 0, nh * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_done, 0, nh * 4, s));
-    CD_CHECK(cudaMemsetAsync(g->hub_idx, 0xff, g->n * 4, s));
     CD_CHECK(cudaMemsetAsync(g->hub_bits, 0, (g->n + 31) / 32 * 4, s));
-    CD_LAUNCH(k_hub_index<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
-                                                                       g->hub_idx, g->hub_bits));
+    CD_LAUNCH(k_hub_bits<<<(unsigned)((nh + 255) / 256), 256, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
+                                                                      g->hub_bits));
+    CD_LAUNCH(k_hub_pref<<<grid_for((g->n + 31) / 32), NT, 0, s>>>(g->bin_list + g->bin_start[B_HUB], nh,
+                                                                   (g->n + 31) / 32, g->hub_pref));
     CD_CHECK(cudaStreamSynchronize(s));  // the host vectors above die here
   }
   {

@@ -113,7 +113,7 @@ struct ScanCtx {
   int32_t* mv_a;
   // hubs
   const int32_t* hub_list;
-  const int32_t* hub_idx;
+  const uint32_t* hub_pref;
   const uint32_t* hub_bits;
   const int64_t* hub_tab;
   unsigned long long* hub_slot;
@@ -410,8 +410,10 @@ __device__ __forceinline__ void hub_slot_read(const ScanCtx& s, int64_t base, in
 // w) changes u's histogram if u is a hub. The hub bitmap (n bits) stays in L2.
 __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u, int32_t A, int32_t c,
                                                     int64_t w) {
-  if (!s.hub_upd || !((__ldg(&s.hub_bits[u >> 5]) >> (u & 31)) & 1u)) return;
-  const int32_t h = s.hub_idx[u];
+  if (!s.hub_upd) return;
+  const uint32_t bits = __ldg(&s.hub_bits[u >> 5]);
+  if (!((bits >> (u & 31)) & 1u)) return;
+  const int32_t h = (int32_t)(__ldg(&s.hub_pref[u >> 5]) + __popc(bits & ((1u << (u & 31)) - 1u)));
   hub_hist_add<false>(s, h, A, -w);
   hub_hist_add<false>(s, h, c, w);
 }
@@ -1453,7 +1455,7 @@ __global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __rest
       while (i >= bb.b[bin + 1]) ++bin;
     }
     if (bin == B_HUB) {
-      const int32_t h = s.hub_idx[v];
+      const int32_t h = (int32_t)(i - bb.b[B_HUB]);  // hub h is the h-th entry of the hub bin
       if (s.hub_tab[h + 1] - s.hub_tab[h] <= HUB_SMALL) {
         small[atomicAdd(&cnt[NBINS + 1], 1ull)] = h;
       } else {
@@ -1894,7 +1896,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     s.singleton_rule = o.singleton_rule;
     s.mv_a = g->mv_a;
     s.hub_list = g->bin_list + g->bin_start[B_HUB];
-    s.hub_idx = g->hub_idx;
+    s.hub_pref = g->hub_pref;
     s.hub_bits = g->hub_bits;
     s.hub_tab = g->hub_tab;
     s.hub_slot = g->hub_slot;
