@@ -480,8 +480,8 @@ def run_serve(args, rank, world, local, steps=None, warmup=None, workload=None, 
     import paper_2507_06471_gb300 as cd
 
     cd.lib()
-    steps = steps if steps is None else steps
-    warmup = warmup if warmup is None else warmup
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     workload = workload or args.workload
     reqs = serve_requests(workload, 11 + 7919 * rank, requests or args.serve_requests)
     torch.cuda.synchronize()
@@ -588,8 +588,8 @@ def run_batch(args, rank, world, local, steps=None, warmup=None):
     import synth
 
     cd.lib()
-    steps = steps if steps is None else steps
-    warmup = warmup if warmup is None else warmup
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     specs = synth.batch_specs(4096, seed=4 + 4096 * rank)
     g, vstart, _ = synth.sbm_batch_device(specs)
     torch.cuda.synchronize()
@@ -604,8 +604,9 @@ def run_batch(args, rank, world, local, steps=None, warmup=None):
     tw, th = cd.cd_autotune(h, cd.cd_params_default(), 3)
     cd.cd_graph_free(h)
 
-    def step(timing=False):
+    def step(timing=False, device_loop=1):
         params.timing = 1 if timing else 0
+        params.device_loop = device_loop
         h = cd.cd_csr_upload(g.off, g.cols, g.w)
         cd.cd_graph_set_bins(h, tw, th)
         cd.cd_graph_set_batches(h, vstart)
@@ -625,11 +626,9 @@ def run_batch(args, rank, world, local, steps=None, warmup=None):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     arcs = 0
-    prof = {}
-    for _ in range(steps):
-        a, rounds, levels, q, p = step(timing=True)
+    for _ in range(steps):  # the rounds after the first of each level run as one captured graph
+        a, rounds, levels, q, _ = step()
         arcs += a
-        merge_profiles(prof, p)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -637,6 +636,19 @@ def run_batch(args, rank, world, local, steps=None, warmup=None):
     clk = clocks.stop()
     ms = allreduce_max(ev0.elapsed_time(ev1), world)
     graphs_per_s = allreduce_sum(float(B * steps), world) / (ms / 1e3)
+    # the same steps with one host read-back per round, for comparison
+    step(device_loop=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(device_loop=0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    host_loop_gps = B * steps / (e0.elapsed_time(e1) / 1e3)
+    # per-kernel shares from one more step with per-kernel events (untimed)
+    prof = {}
+    merge_profiles(prof, step(timing=True)[4])
 
     # one call per graph (upload + cd_louvain_run) on an evenly spaced sample
     members = synth.unpack_batch(g, vstart)
@@ -676,7 +688,12 @@ def run_batch(args, rank, world, local, steps=None, warmup=None):
             "max_levels_reached": int(levels.max()), "mean_q": float(np.mean(q)),
             "solo": {"graphs_per_s": solo_gps, "sample": int(len(pick)), "same_labels_as_batched": same,
                      "how": "cd_csr_upload + cd_louvain_run per graph, one graph at a time"},
-            "speedup_vs_solo": graphs_per_s / solo_gps, "kernels": kernels, "gpu_launches": launches,
+            "speedup_vs_solo": graphs_per_s / solo_gps,
+            "host_loop": {"graphs_per_s": host_loop_gps,
+                          "how": "the same calls with device_loop = 0 (one host read-back per round)"},
+            "kernels": kernels, "gpu_launches": launches,
+            "gpu_launches_note": "host launch calls; each level's rounds after the first are one graph "
+                                 "launch whose body kernels run once per round",
             "clocks": clk}
     return line
 
@@ -695,7 +712,8 @@ def compact_many(line):
     """The parts of a batched or served line carried inside the R-MAT line."""
     keep = ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "config", "gteps",
             "louvain_rounds", "mean_q", "solo", "speedup_vs_solo", "latency_ms_all_at_once", "open_loop",
-            "mean_batched_with", "one_at_a_time", "speedup_vs_one_at_a_time", "e2e", "gpu_launches", "clocks")
+            "mean_batched_with", "one_at_a_time", "speedup_vs_one_at_a_time", "host_loop", "e2e", "gpu_launches",
+            "clocks")
     return {k: line[k] for k in keep if k in line}
 
 

@@ -68,6 +68,15 @@ typedef struct cd_params {
                                (the deferral coin still applies: without it adjacent vertices swap
                                labels in lockstep); results vary from run to run. 0 (default):
                                synchronous rounds, reproducible */
+  int32_t device_loop;      /* Where the round loop runs. 1 (default): in batched runs (cd_batch_*) the
+                               rounds after the first of a run or Louvain level run as one captured CUDA
+                               graph (a conditional WHILE node whose body is one round; the round number,
+                               the stop tests and the trace stay on the device), so a level costs one
+                               graph launch and no per-round host synchronisation; other runs keep the
+                               host loop (building a graph per level costs more than the few round trips
+                               of a small graph saves). 2: every run uses the device loop. 0: the host
+                               loop everywhere (one read-back per round). Results are identical in every
+                               mode; timing = 1 always uses the host loop (it records per-round events) */
 } cd_params;
 
 /* Per-round record of the last run on a graph (cd_trace_get). */

@@ -40,7 +40,8 @@ class cd_params(ctypes.Structure):
                 ("threshold", ctypes.c_int64), ("tie_keep_current", ctypes.c_int32),
                 ("singleton_rule", ctypes.c_int32), ("use_frontier", ctypes.c_int32),
                 ("timing", ctypes.c_int32), ("sched_seed", ctypes.c_uint64),
-                ("aggregation", ctypes.c_int32), ("asynchronous", ctypes.c_int32)]
+                ("aggregation", ctypes.c_int32), ("asynchronous", ctypes.c_int32),
+                ("device_loop", ctypes.c_int32)]
 
 
 class cd_round_trace(ctypes.Structure):

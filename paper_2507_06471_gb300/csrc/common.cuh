@@ -213,6 +213,8 @@ struct RunOpts {
   int32_t level;
   int async_mode = 0;  // committed moves take effect at once (the coin still defers half of them)
   bool singleton_start = false;  // the run starts from C[v] = v (Sigma_tot = deg_w, sizes 1)
+  bool device_loop = false;      // rounds after the first run as one captured graph (batched runs)
+  bool device_loop_all = false;  // ... in every run
 };
 // Algorithm 1 / Algorithm 2 round loops on g->C (device). Louvain: g->C holds
 // the initial partition; sigma/csize are rebuilt from it.

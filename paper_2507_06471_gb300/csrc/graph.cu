@@ -787,6 +787,7 @@ int cd_params_default(cd_params* p) {
   p->sched_seed = 0x5EED5EEDull;
   p->aggregation = 0;
   p->asynchronous = 0;
+  p->device_loop = 1;
   return CD_OK;
 }
 

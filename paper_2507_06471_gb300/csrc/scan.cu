@@ -151,6 +151,10 @@ struct ScanCtx {
   int32_t* C_w;
   int64_t* sigma_w;  // null for LPA
   int32_t* csize_w;
+  // device-side round loop: the round number and the hub-update switch are
+  // read from device memory (null: the host-side values above apply)
+  const int32_t* round_p;
+  const int32_t* hub_upd_p;
   // batched mode (gid == nullptr: one graph)
   const int32_t* gid;
   const int64_t* gbase;
@@ -158,6 +162,11 @@ struct ScanCtx {
   const uint8_t* gfrozen;
   unsigned long long* gcnt;
 };
+
+__device__ __forceinline__ int round_of(const ScanCtx& s) { return s.round_p ? *s.round_p : s.round; }
+__device__ __forceinline__ bool hub_upd_of(const ScanCtx& s) {
+  return s.hub_upd_p ? *s.hub_upd_p != 0 : s.hub_upd != 0;
+}
 
 // Flag vertex u for the next round (a bit in an L2-resident bitmap).
 __device__ __forceinline__ void flag_next(const ScanCtx& s, int32_t u) {
@@ -246,7 +255,7 @@ __device__ __forceinline__ int act_single(const ScanCtx& s, int32_t v, int32_t c
   if (target == cur) return 0;
   if (s.mark) flag_next(s, v);
   count_change(s, v);
-  if (commit_coin(s.seed, s.level, s.round, local_id(s, v))) {
+  if (commit_coin(s.seed, s.level, round_of(s), local_id(s, v))) {
     unsigned long long pos = atomicAdd(&s.ctr[C_MOVES], 1ull);
     s.mv_v[pos] = v;
     s.mv_c[pos] = target;
@@ -410,7 +419,7 @@ __device__ __forceinline__ void hub_slot_read(const ScanCtx& s, int64_t base, in
 // w) changes u's histogram if u is a hub. The hub bitmap (n bits) stays in L2.
 __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u, int32_t A, int32_t c,
                                                     int64_t w) {
-  if (!s.hub_upd) return;
+  if (!hub_upd_of(s)) return;
   const uint32_t bits = __ldg(&s.hub_bits[u >> 5]);
   if (!((bits >> (u & 31)) & 1u)) return;
   const int32_t h = (int32_t)(__ldg(&s.hub_pref[u >> 5]) + __popc(bits & ((1u << (u & 31)) - 1u)));
@@ -467,7 +476,7 @@ __global__ void __launch_bounds__(NT, 6) k_scan_tile(ScanCtx s, const int32_t* _
     int32_t target = cur;
     if (act) target = decide<LOUV, NK>(s, v, cur, bk, bc, cm != 0, kcur, volv);
     const bool want = act && target != cur;
-    const bool commit = want && commit_coin(s.seed, s.level, s.round, local_id(s, v));
+    const bool commit = want && commit_coin(s.seed, s.level, round_of(s), local_id(s, v));
     if (want && sub == 0) count_change(s, v);
     const unsigned am = __ballot_sync(FULL, commit && sub == 0);
     if (am) {
@@ -820,7 +829,7 @@ __global__ void __launch_bounds__(256, (LOUV || !W::unit) ? 4 : 5)
     int32_t target = h.cur;
     if (h.act) target = decide<LOUV, NK>(s, my_v, h.cur, my_bk, my_bc, my_hc, my_kc, h.vol);
     const bool want = h.act && target != h.cur;
-    const bool commit = want && commit_coin(s.seed, s.level, s.round, local_id(s, my_v));
+    const bool commit = want && commit_coin(s.seed, s.level, round_of(s), local_id(s, my_v));
     if (want) count_change(s, my_v);
     const unsigned cm = __ballot_sync(FULL, commit);
     if (cm) {
@@ -1429,6 +1438,91 @@ __global__ void __launch_bounds__(NT) k_first_round(ScanCtx s, const int32_t* __
   flush_counters(s, bin, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
+// ------------------------------------------------------------------ device-side round loop
+//
+// After round 0, the remaining rounds of a run or level can run as one
+// captured CUDA graph: a conditional WHILE node whose body is one round. Every
+// value the host loop decides per round lives in device memory instead: the
+// round number (the coin reads it), whether this round's moves update the hub
+// histograms, the trace row, the move totals and the stop test, which clears
+// the loop condition.
+struct DevLoop {
+  int32_t round;    // the round being run
+  int32_t hub_upd;  // this round's committed moves update the hub histograms
+  int32_t max_iter;
+  int32_t pad;
+  long long prev_moves;
+  long long total_moves;
+  unsigned long long alive;  // per-graph stop: graphs still running after this round
+};
+constexpr int TRACE_W = 6;  // trace row: examined, arcs, moved, deferred, candidate pairs, moved arcs
+
+__global__ void k_loop_begin(DevLoop* dl, int64_t n, int64_t div, int has_hubs) {
+  dl->hub_upd = (has_hubs && dl->prev_moves * div > n) ? 0 : 1;
+}
+
+// A round whose moves did not update the hub histograms queues every hub for
+// a rebuild at the start of the next one.
+__global__ void k_queue_all(ScanCtx s, const DevLoop* dl) {
+  if (dl->hub_upd) return;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < s.nhubs; h += stride) {
+    s.hub_rb[h] = HUB_REBUILD;
+    s.hub_flist_w[h] = (int32_t)h;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *s.hub_fcnt_w = (unsigned long long)s.nhubs;
+}
+
+// The hubs flagged this round become the list the next round's preparation reads.
+__global__ void k_flist_carry(const int32_t* __restrict__ flist_w, const unsigned long long* fcnt_w,
+                              int32_t* __restrict__ flist_r, unsigned long long* fcnt_r) {
+  const int64_t nf = (int64_t)*(volatile const unsigned long long*)fcnt_w;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += stride) flist_r[i] = flist_w[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *fcnt_r = (unsigned long long)nf;
+}
+
+// Batched runs that stop per graph: a graph stops after its own round with at
+// most `threshold` vertices wanting to move (moved + deferred).
+__global__ void k_loop_freeze(const unsigned long long* __restrict__ gcnt, uint8_t* gfrozen, int32_t* grounds,
+                              int64_t nb, DevLoop* dl, int64_t threshold) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  unsigned long long alive = 0;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += stride) {
+    if (gfrozen[b]) continue;
+    if ((int64_t)gcnt[b] <= threshold) {
+      gfrozen[b] = 1;
+      grounds[b] = dl->round + 1;
+    } else {
+      ++alive;
+    }
+  }
+  if (alive) atomicAdd(&dl->alive, alive);
+}
+
+__global__ void k_loop_end(const unsigned long long* __restrict__ ctr, DevLoop* dl, long long* trace, int louv,
+                           int64_t threshold, int per_graph, int64_t iso_add, cudaGraphConditionalHandle handle) {
+  const long long moves = (long long)ctr[C_MOVES], deferred = (long long)ctr[C_DEFERRED];
+  long long act = 0, arcs = 0, cands = 0;
+  for (int b = 0; b < NBINS; ++b) {
+    act += (long long)ctr[C_BIN0 + 3 * b];
+    arcs += (long long)ctr[C_BIN0 + 3 * b + 1];
+    cands += (long long)ctr[C_BIN0 + 3 * b + 2];
+  }
+  long long* t = trace + (int64_t)TRACE_W * dl->round;
+  t[0] = act + iso_add;
+  t[1] = arcs;
+  t[2] = moves;
+  t[3] = deferred;
+  t[4] = cands;
+  t[5] = (long long)ctr[C_MARCS];
+  dl->prev_moves = moves;
+  dl->total_moves += moves;
+  const bool stop = per_graph ? dl->alive == 0 : (louv ? moves + deferred == 0 : moves + deferred <= threshold);
+  dl->round += 1;
+  if (stop || dl->round >= dl->max_iter) cudaGraphSetConditional(handle, 0);
+}
+
 // ------------------------------------------------------------------ frontier
 
 struct BinBounds {
@@ -1503,9 +1597,10 @@ __device__ __forceinline__ void warp_add_community(int64_t* sigma, int32_t* csiz
 }
 
 template <bool LOUV>
-__global__ void __launch_bounds__(NT) k_apply_state(ScanCtx s, int64_t nmoves, int64_t* sigma,
-                                                    int32_t* csize, int32_t* C) {
+__global__ void __launch_bounds__(NT) k_apply_state(ScanCtx s, const unsigned long long* __restrict__ nmoves_p,
+                                                    int64_t* sigma, int32_t* csize, int32_t* C) {
   __shared__ int64_t stage[NW][32];
+  const int64_t nmoves = (int64_t)*nmoves_p;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t stride = (int64_t)gridDim.x * NT;
   // whole warps iterate together (the match needs every lane)
@@ -1566,8 +1661,10 @@ __global__ void k_sigma32_all(const int64_t* __restrict__ sigma, int64_t n, uint
 
 // After the moves of a round are applied: refresh the copies of the
 // communities they touched (plain stores of the final values).
-__global__ void k_sigma32_moves(const int32_t* __restrict__ mv_a, const int32_t* __restrict__ mv_c, int64_t nmoves,
+__global__ void k_sigma32_moves(const int32_t* __restrict__ mv_a, const int32_t* __restrict__ mv_c,
+                                const unsigned long long* __restrict__ nmoves_p,
                                 const int64_t* __restrict__ sigma, uint32_t* __restrict__ s32) {
+  const int64_t nmoves = (int64_t)*nmoves_p;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; m < nmoves; m += stride) {
     const int32_t a = mv_a[m], c = mv_c[m];
@@ -1816,6 +1913,258 @@ int dispatch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned
              : launch_round<LOUV, WI64, unsigned long long, NK>(g, s, lists, counts, marks);
 }
 
+// The parts of a round's context that do not change from round to round.
+ScanCtx static_ctx(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool per_graph_stop) {
+  ScanCtx s;
+  s.off = g->off;
+  s.cols = g->cols;
+  s.w = g->w;
+  s.degw = g->degw;
+  s.vol = g->vol;
+  s.C = g->C;
+  s.sigma = g->sigma;
+  s.sigma32 = use_s32 ? g->sigma32 : nullptr;
+  s.csize = g->csize;
+  s.all_active = o.use_frontier ? 0 : 1;
+  s.mark = o.use_frontier ? 1 : 0;
+  s.mv_v = g->mv_v;
+  s.mv_c = g->mv_c;
+  s.ctr = (unsigned long long*)g->ctr;
+  s.status = g->status;
+  s.seed = o.sched_seed;
+  s.level = o.level;
+  s.tie_keep = o.tie_keep_current;
+  s.singleton_rule = o.singleton_rule;
+  s.mv_a = g->mv_a;
+  s.hub_list = g->bin_list + g->bin_start[B_HUB];
+  s.hub_pref = g->hub_pref;
+  s.hub_bits = g->hub_bits;
+  s.hub_tab = g->hub_tab;
+  s.hub_slot = g->hub_slot;
+  s.hub_wide = g->hub_wide;
+  s.hub_item_hub = g->hub_item_hub;
+  s.hub_item_arc = g->hub_item_arc;
+  s.hub_ev_hub = g->hub_ev_hub;
+  s.hub_ev_slot = g->hub_ev_slot;
+  s.hub_ev_first = g->hub_ev_first;
+  s.hub_part = g->hub_part;
+  s.hub_cur = g->hub_cur;
+  s.hub_hascur = g->hub_hascur;
+  s.hub_done = g->hub_done;
+  s.hub_mv = g->hub_mv;
+  s.hub_rb = g->hub_rb;
+  s.hub_used = g->hub_used;
+  s.hub_item_first = g->hub_item_first;
+  s.hub_blist = g->hub_blist;
+  s.hub_mlist = g->hub_mlist;
+  s.hub_lcnt = g->hub_lcnt;
+  s.hub_cl = g->hub_cl;
+  s.hub_ccnt = g->hub_ccnt;
+  s.n_items = g->hub_items;
+  s.nhubs = g->nhubs;
+  s.n_ev_items = g->hub_eval_items;
+  s.async_mode = o.async_mode;
+  s.C_w = g->C;
+  s.sigma_w = louv ? g->sigma : nullptr;
+  s.csize_w = g->csize;
+  s.gid = o.batched ? g->gid : nullptr;
+  s.gbase = o.batched ? g->gbase : nullptr;
+  s.gvol = o.batched ? g->gvol : nullptr;
+  s.gfrozen = o.batched ? g->gfrozen : nullptr;
+  s.gcnt = per_graph_stop ? (unsigned long long*)g->gcnt : nullptr;
+  s.round_p = nullptr;
+  s.hub_upd_p = nullptr;
+  s.hub_upd = 1;
+  return s;
+}
+
+// Rounds from `r0` on as one graph launch (see the device-side round loop
+// above). fcur/fnxt: the flag bitmaps as left by the host loop; the hubs
+// flagged by round r0 - 1 are in list (r0 - 1) & 1 of hub_flist.
+int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool per_graph_stop, int32_t r0,
+                  uint32_t* fcur, uint32_t* fnxt, int64_t prev_moves, int64_t& total_moves, int32_t& rounds,
+                  std::vector<int32_t>* graph_rounds) {
+  const cudaStream_t st = g->stream;
+  const int64_t n = g->n, nh = g->nhubs;
+  const size_t fbytes = (size_t)((n + 31) / 32) * 4;
+  DevLoop* dl = nullptr;
+  long long* trace = nullptr;
+  int32_t* grounds = nullptr;
+  int rc;
+  if ((rc = dev_alloc_t(&dl, 1, st)) || (rc = dev_alloc_t(&trace, (int64_t)TRACE_W * o.max_iter, st)) ||
+      (per_graph_stop && (rc = dev_alloc_t(&grounds, g->nb, st)))) {
+    dev_free(dl, st);
+    dev_free(trace, st);
+    return rc;
+  }
+  DevLoop h0{};
+  h0.round = r0;
+  h0.hub_upd = 1;
+  h0.max_iter = o.max_iter;
+  h0.prev_moves = prev_moves;
+  h0.total_moves = total_moves;
+  CD_CHECK(cudaMemcpyAsync(dl, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+  if (per_graph_stop)
+    CD_CHECK(cudaMemcpyAsync(grounds, graph_rounds->data(), g->nb * 4, cudaMemcpyHostToDevice, st));
+  // the flagged-hub lists: the body reads list A (what the previous round
+  // wrote) and writes list B, then carries B to A
+  int32_t* listA = nh > 0 ? g->hub_flist + ((r0 - 1) & 1) * nh : nullptr;
+  int32_t* listB = nh > 0 ? g->hub_flist + (r0 & 1) * nh : nullptr;
+  unsigned long long* cntA = nh > 0 ? g->hub_fcnt + ((r0 - 1) & 1) : nullptr;
+  unsigned long long* cntB = nh > 0 ? g->hub_fcnt + (r0 & 1) : nullptr;
+  ScanCtx s = static_ctx(g, o, louv, use_s32, per_graph_stop);
+  s.flag_cur = fcur;
+  s.flag_nxt = fnxt;
+  s.round = r0;
+  s.round_p = &dl->round;
+  s.hub_upd_p = &dl->hub_upd;
+  s.hub_flist_w = listB;
+  s.hub_fcnt_w = cntB;
+  s.hub_flist_r = listA;
+  s.hub_fcnt_r = cntA;
+  const bool compact = o.use_frontier && g->bin_start[NBINS] > 0;
+  const int32_t* lists = compact ? g->act_list : g->bin_list;
+  const unsigned long long* counts = compact ? g->act_cnt : g->full_cnt;
+  s.ev_list = compact ? g->act_ev : g->hub_big_items;
+  s.ev_cnt = (compact ? g->act_cnt : g->full_cnt) + NBINS;
+  s.small_list = compact ? g->act_small : g->hub_small;
+  s.small_cnt = (compact ? g->act_cnt : g->full_cnt) + NBINS + 1;
+  const bool v32 = g->max_degw < ((int64_t)1 << 32);
+
+  cudaGraph_t graph = nullptr, body = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // capture happens on a stream of this thread's own (never the legacy
+  // default stream, which cannot be captured); the graph runs on g->stream
+  static thread_local cudaStream_t cap = nullptr;
+  cudaGraphConditionalHandle handle;
+  auto cleanup = [&]() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  };
+  cudaError_t e = cap ? cudaSuccess : cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+  }
+  if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cleanup();
+    dev_free(dl, st);
+    dev_free(trace, st);
+    dev_free(grounds, st);
+    return set_cuda_error(e);
+  }
+  // one round, enqueued on the capture stream (the launch helpers use g->stream)
+  g->stream = cap;
+  rc = [&]() -> int {
+    CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), cap));
+    if (per_graph_stop) {
+      CD_CHECK(cudaMemsetAsync(g->gcnt, 0, g->nb * sizeof(int64_t), cap));
+      CD_CHECK(cudaMemsetAsync(&dl->alive, 0, sizeof(unsigned long long), cap));
+    }
+    if (o.use_frontier && n > 0) CD_CHECK(cudaMemsetAsync(fnxt, 0, fbytes, cap));
+    if (nh > 0) {
+      CD_CHECK(cudaMemsetAsync(g->hub_mv, 0, 3 * nh * sizeof(int32_t), cap));
+      CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), cap));
+      CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), cap));
+      CD_CHECK(cudaMemsetAsync(cntB, 0, sizeof(unsigned long long), cap));
+    }
+    CD_LAUNCH(k_loop_begin<<<1, 1, 0, cap>>>(dl, n, louv ? HUB_SKIP_DIV : HUB_SKIP_DIV_LPA, nh > 0));
+    if (compact) {
+      CD_CHECK(cudaMemsetAsync(g->act_cnt, 0, (NBINS + 2) * sizeof(unsigned long long), cap));
+      BinBounds bb;
+      for (int b = 0; b <= NBINS; ++b) bb.b[b] = g->bin_start[b];
+      CD_LAUNCH(k_compact<<<wave_grid(k_compact, NT, 0, (g->bin_start[NBINS] + NT - 1) / NT), NT, 0, cap>>>(
+          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev, g->act_small));
+    }
+    std::vector<std::pair<size_t, int>> marks;
+    int rc2;
+    if (louv) {
+      if (g->vol < ((int64_t)1 << 31)) rc2 = dispatch_round<true, true>(g, s, lists, counts, marks, v32);
+      else rc2 = dispatch_round<true, false>(g, s, lists, counts, marks, v32);
+    } else {
+      rc2 = dispatch_round<false, false>(g, s, lists, counts, marks, v32);
+    }
+    if (rc2) return rc2;
+    const unsigned ga = grid_cap(n > 0 ? (n + NT - 1) / NT : 1, 152 * 8);
+    if (!o.async_mode) {  // asynchronous moves were applied when made
+      if (louv) {
+        CD_LAUNCH(k_apply_state<true><<<ga, NT, 0, cap>>>(s, s.ctr + C_MOVES, g->sigma, g->csize, g->C));
+        if (use_s32)
+          CD_LAUNCH(k_sigma32_moves<<<ga, NT, 0, cap>>>(g->mv_a, g->mv_c, s.ctr + C_MOVES, g->sigma, g->sigma32));
+      } else {
+        CD_LAUNCH(k_apply_state<false><<<ga, NT, 0, cap>>>(s, s.ctr + C_MOVES, g->sigma, g->csize, g->C));
+      }
+    }
+    if (nh > 0) {
+      const unsigned gh = grid_cap(g->hub_items, 152 * 8);
+      if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, cap>>>(s));
+      else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, cap>>>(s));
+      else CD_LAUNCH(k_hub_mark<WI64><<<gh, NT, 0, cap>>>(s));
+      CD_LAUNCH(k_queue_all<<<grid_cap((nh + NT - 1) / NT), NT, 0, cap>>>(s, dl));
+      CD_LAUNCH(k_flist_carry<<<grid_cap((nh + NT - 1) / NT), NT, 0, cap>>>(listB, cntB, listA, cntA));
+    }
+    if (per_graph_stop)
+      CD_LAUNCH(k_loop_freeze<<<grid_cap((g->nb + NT - 1) / NT), NT, 0, cap>>>(
+          (const unsigned long long*)g->gcnt, g->gfrozen, grounds, g->nb, dl, o.threshold));
+    CD_LAUNCH(k_loop_end<<<1, 1, 0, cap>>>(s.ctr, dl, trace, louv ? 1 : 0, o.threshold, per_graph_stop ? 1 : 0,
+                                           o.use_frontier ? 0 : g->n_isolated, handle));
+    if (o.use_frontier && n > 0) CD_CHECK(cudaMemcpyAsync(fcur, fnxt, fbytes, cudaMemcpyDeviceToDevice, cap));
+    CD_CHECK(cudaGetLastError());
+    return CD_OK;
+  }();
+  g->stream = st;
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cap, &captured);
+  if (!rc && e != cudaSuccess) rc = set_cuda_error(e);
+  if (!rc) {
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) rc = set_cuda_error(e);
+    else note_launch();
+  }
+  DevLoop hd{};
+  std::vector<long long> ht;
+  if (!rc) {
+    ht.resize((size_t)TRACE_W * o.max_iter);
+    CD_CHECK(cudaMemcpyAsync(&hd, dl, sizeof(hd), cudaMemcpyDeviceToHost, st));
+    CD_CHECK(cudaMemcpyAsync(ht.data(), trace, ht.size() * 8, cudaMemcpyDeviceToHost, st));
+    if (per_graph_stop)
+      CD_CHECK(cudaMemcpyAsync(graph_rounds->data(), grounds, g->nb * 4, cudaMemcpyDeviceToHost, st));
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = CD_ECUDA;
+  }
+  cleanup();
+  dev_free(dl, st);
+  dev_free(trace, st);
+  dev_free(grounds, st);
+  if (rc) return rc;
+  for (int32_t r = r0; r < hd.round; ++r) {
+    const long long* t = ht.data() + (size_t)TRACE_W * r;
+    cd_round_trace tr;
+    tr.level = o.level;
+    tr.round = r;
+    tr.active = t[0];
+    tr.arcs = t[1];
+    tr.moved = t[2];
+    tr.deferred = t[3];
+    tr.cands = t[4];
+    tr.moved_arcs = t[5];
+    tr.scan_ms = tr.round_ms = 0.f;
+    g->trace.push_back(tr);
+  }
+  total_moves = hd.total_moves;
+  rounds = hd.round;
+  return CD_OK;
+}
+
 int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int32_t* rounds_out,
                std::vector<int32_t>* graph_rounds = nullptr) {
   cudaStream_t st = g->stream;
@@ -1860,7 +2209,15 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   if (g->timing)
     for (auto& e : ev) cudaEventCreate(&e);
+  // rounds after the first as one captured graph (a device-side loop) unless
+  // per-round events are wanted
+  const bool dev_loop = o.device_loop && !g->timing && (o.batched || o.device_loop_all);
   for (int32_t r = 0; r < o.max_iter && rc == CD_OK; ++r) {
+    if (r > 0 && dev_loop) {
+      rc = device_rounds(g, o, louv, use_s32, per_graph_stop, r, fcur, fnxt, prev_moves, total_moves, rounds,
+                         graph_rounds);
+      break;
+    }
     if (g->timing) cudaEventRecord(ev[0], st);
     CD_CHECK(cudaMemsetAsync(g->ctr, 0, C_COUNT * sizeof(int64_t), st));
     if (per_graph_stop) CD_CHECK(cudaMemsetAsync(g->gcnt, 0, g->nb * sizeof(int64_t), st));
@@ -1871,61 +2228,14 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
     }
-    ScanCtx s;
-    s.off = g->off;
-    s.cols = g->cols;
-    s.w = g->w;
-    s.degw = g->degw;
-    s.vol = g->vol;
-    s.C = g->C;
-    s.sigma = g->sigma;
-    s.sigma32 = use_s32 ? g->sigma32 : nullptr;
-    s.csize = g->csize;
+    ScanCtx s = static_ctx(g, o, louv, use_s32, per_graph_stop);
     s.flag_cur = fcur;
     s.flag_nxt = fnxt;
-    s.all_active = o.use_frontier ? 0 : 1;
-    s.mark = o.use_frontier ? 1 : 0;
-    s.mv_v = g->mv_v;
-    s.mv_c = g->mv_c;
-    s.ctr = (unsigned long long*)g->ctr;
-    s.status = g->status;
-    s.seed = o.sched_seed;
-    s.level = o.level;
     s.round = r;
-    s.tie_keep = o.tie_keep_current;
-    s.singleton_rule = o.singleton_rule;
-    s.mv_a = g->mv_a;
-    s.hub_list = g->bin_list + g->bin_start[B_HUB];
-    s.hub_pref = g->hub_pref;
-    s.hub_bits = g->hub_bits;
-    s.hub_tab = g->hub_tab;
-    s.hub_slot = g->hub_slot;
-    s.hub_wide = g->hub_wide;
-    s.hub_item_hub = g->hub_item_hub;
-    s.hub_item_arc = g->hub_item_arc;
-    s.hub_ev_hub = g->hub_ev_hub;
-    s.hub_ev_slot = g->hub_ev_slot;
-    s.hub_ev_first = g->hub_ev_first;
-    s.hub_part = g->hub_part;
-    s.hub_cur = g->hub_cur;
-    s.hub_hascur = g->hub_hascur;
-    s.hub_done = g->hub_done;
-    s.hub_mv = g->hub_mv;
-    s.hub_rb = g->hub_rb;
-    s.hub_used = g->hub_used;
-    s.hub_item_first = g->hub_item_first;
-    s.hub_blist = g->hub_blist;
-    s.hub_mlist = g->hub_mlist;
-    s.hub_lcnt = g->hub_lcnt;
-    s.hub_cl = g->hub_cl;
-    s.hub_ccnt = g->hub_ccnt;
     s.hub_flist_w = g->hub_flist ? g->hub_flist + (r & 1) * g->nhubs : nullptr;
     s.hub_fcnt_w = g->hub_fcnt ? g->hub_fcnt + (r & 1) : nullptr;
     s.hub_flist_r = g->hub_flist ? g->hub_flist + ((r + 1) & 1) * g->nhubs : nullptr;
     s.hub_fcnt_r = g->hub_fcnt ? g->hub_fcnt + ((r + 1) & 1) : nullptr;
-    s.n_items = g->hub_items;
-    s.nhubs = g->nhubs;
-    s.n_ev_items = g->hub_eval_items;
     // In a round that moves many vertices (the first of a run or level, or
     // after one that moved more than 1/HUB_SKIP_DIV of them, 1/4 for LPA) the hub
     // histograms are not updated move by move: every hub is rebuilt from its
@@ -1934,15 +2244,6 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     const bool skip_upd =
         g->nhubs > 0 && (r == 0 || prev_moves * (louv ? HUB_SKIP_DIV : HUB_SKIP_DIV_LPA) > n);
     s.hub_upd = skip_upd ? 0 : 1;
-    s.async_mode = o.async_mode;
-    s.C_w = g->C;
-    s.sigma_w = louv ? g->sigma : nullptr;
-    s.csize_w = g->csize;
-    s.gid = o.batched ? g->gid : nullptr;
-    s.gbase = o.batched ? g->gbase : nullptr;
-    s.gvol = o.batched ? g->gvol : nullptr;
-    s.gfrozen = o.batched ? g->gfrozen : nullptr;
-    s.gcnt = per_graph_stop ? (unsigned long long*)g->gcnt : nullptr;
     // the round's work lists: every listed vertex in round 0 (or without a
     // frontier), else the active ones, compacted
     const int32_t* lists = g->bin_list;
@@ -2015,12 +2316,12 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
         KTimer t(g, K_APPLY, (double)moves * (8 + 4 + (louv ? 8 + 16 + 8 : 0)));
         const unsigned gt = grid_cap((moves + NT - 1) / NT);
         if (louv) {
-          CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+          CD_LAUNCH(k_apply_state<true><<<gt, NT, 0, st>>>(s, s.ctr + C_MOVES, g->sigma, g->csize, g->C));
           if (use_s32)
-            CD_LAUNCH(k_sigma32_moves<<<gt, NT, 0, st>>>(g->mv_a, g->mv_c, moves, g->sigma, g->sigma32));
+            CD_LAUNCH(k_sigma32_moves<<<gt, NT, 0, st>>>(g->mv_a, g->mv_c, s.ctr + C_MOVES, g->sigma, g->sigma32));
         }
         else
-          CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, moves, g->sigma, g->csize, g->C));
+          CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, s.ctr + C_MOVES, g->sigma, g->csize, g->C));
       }
       if (g->nhubs > 0) {
         KTimer t(g, K_HUB_MARK);
@@ -2147,6 +2448,8 @@ RunOpts opts_from(const cd_params* p, int32_t level) {
   o.sched_seed = p->sched_seed;
   o.level = level;
   o.async_mode = p->asynchronous ? 1 : 0;
+  o.device_loop = p->device_loop != 0;
+  o.device_loop_all = p->device_loop == 2;
   return o;
 }
 

@@ -442,3 +442,41 @@ def test_key_width_boundary(target):
     olab, olv, oq, _ = oracle.louvain(off, cols, w)
     assert levels == olv and np.array_equal(lab.cpu().numpy(), olab)
     assert abs(q - oq) <= 1e-12 * max(1.0, abs(oq))
+
+
+@pytest.mark.parametrize("name", ["sbm10k", "rmat16", "bins_w", "lfr50k_w", "loops_w"])
+def test_device_loop_equals_host_loop(name):
+    """Rounds after the first run as one captured graph with a device-side
+    loop (device_loop = 2) or one host read-back per round (device_loop = 0):
+    labels, round counts and every trace field agree."""
+    g = graph(name)
+    G = upload(g)
+    keys = ("level", "round", "active", "arcs", "moved", "deferred", "cands", "moved_arcs")
+
+    def runs(dl):
+        lab1, r1 = G.lpa(device_loop=dl)
+        t1 = [{k: t[k] for k in keys} for t in G.trace()]
+        lab2, lv, q = G.louvain(device_loop=dl)
+        t2 = [{k: t[k] for k in keys} for t in G.trace()]
+        return lab1.cpu().numpy(), r1, t1, lab2.cpu().numpy(), lv, q, t2
+
+    a, b = runs(2), runs(0)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[3], b[3])
+    assert a[1] == b[1] and a[2] == b[2] and a[4] == b[4] and a[5] == b[5] and a[6] == b[6]
+
+
+def test_device_loop_batched_rounds_per_graph():
+    graphs = [synth.sbm(n, k, "0.2", "0.002", seed=90 + i, wmax=3)
+              for i, (n, k) in enumerate([(300, 5), (1200, 12), (80, 2), (2000, 30), (50, 3)])]
+    packed, vstart = synth.pack_batch(graphs)
+    G = cd.Graph(packed.off.cuda(), packed.cols.cuda(), packed.w.cuda())
+    G.set_batches(vstart)
+    out = []
+    for dl in (1, 0):
+        lab, rounds = G.batch_lpa(device_loop=dl, threshold=3)
+        lab2, levels, q = G.batch_louvain(device_loop=dl)
+        out.append((lab.cpu().numpy(), list(rounds), lab2.cpu().numpy(), list(levels), list(q)))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    assert out[0][1] == out[1][1] and out[0][3] == out[1][3] and out[0][4] == out[1][4]
