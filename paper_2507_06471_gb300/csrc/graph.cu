@@ -390,6 +390,11 @@ __global__ void k_download_w(const int64_t* __restrict__ off, const int32_t* __r
     }
 }
 
+__global__ void k_narrow_w(const int64_t* __restrict__ w64, int64_t nnz, int32_t* __restrict__ w32) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) w32[e] = (int32_t)w64[e];
+}
+
 __global__ void k_labels_check(const int32_t* __restrict__ lab, int64_t n, int32_t* status) {
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -757,6 +762,18 @@ int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* c
     if (!rc) {
       int st = read_status(g);
       if (st) rc = st;
+    }
+  }
+  // 64-bit weights whose every row sum (loops doubled included) is below 2^31
+  // are kept in 32 bits: every arc weight is at most its row's deg_w
+  if (!rc && g->wkind == W_I64 && g->w && nnz > 0 && stats[3] < (1ull << 31)) {
+    int32_t* w32 = nullptr;
+    rc = dev_alloc_t(&w32, nnz, s);
+    if (!rc) {
+      CD_LAUNCH(k_narrow_w<<<grid_for(nnz), NT, 0, s>>>((const int64_t*)g->w, nnz, w32));
+      dev_free(g->w, s);
+      g->w = w32;
+      g->wkind = W_I32;
     }
   }
   if (!rc) rc = finish_graph(g, stats);
