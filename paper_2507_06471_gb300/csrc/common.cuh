@@ -124,6 +124,9 @@ struct cd_graph {
   unsigned long long* hub_lcnt = nullptr;  // 2: queued build and mark items
   int32_t* hub_cl = nullptr;               // 5 x nhubs: hubs rebuilt per build class
   unsigned long long* hub_ccnt = nullptr;  // 5: their counts
+  unsigned long long* hub_log = nullptr;   // per round: hub-histogram updates (hub, old, new, w) to apply
+  unsigned long long* hub_log_cnt = nullptr;
+  int64_t hub_log_cap = 0;
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
   bool cols_distinct = false;      // no row repeats a column (strictly increasing input rows, or coarse rows)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex

@@ -156,6 +156,7 @@ __global__ void k_offsets_check(const OffT* __restrict__ in, int64_t n, int64_t 
 // and sums a row of at most INGEST_LANE arcs alone; the warp sums the rows of
 // up to INGEST_WARP arcs one at a time with coalesced loads; longer rows are
 // listed for k_ingest_big (a CTA per row).
+constexpr int64_t HUB_LOG_DIV = 4;  // budget of logged hub updates per round: hub arcs / 4
 constexpr int INGEST_LANE = 32;
 constexpr int INGEST_WARP = 4096;
 constexpr int ST_UNSORTED = 4 + NBINS;
@@ -432,6 +433,7 @@ void free_arrays(cd_graph* g) {
                 g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
                 g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
                 g->hub_blist,    g->hub_mlist,     g->hub_lcnt,     g->C,            g->sigma,        g->csize,
+                g->hub_log,      g->hub_log_cnt,
                 g->sigma32,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
                 g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
@@ -449,7 +451,7 @@ void free_bins(cd_graph* g) {
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
                 g->hub_rb,       g->hub_used,     g->hub_item_first, g->hub_blist,
                 g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
-                g->hub_mlist,    g->hub_lcnt};
+                g->hub_mlist,    g->hub_lcnt,     g->hub_log,      g->hub_log_cnt};
   for (void* p : ps) dev_free(p, s);
   g->bin_list = nullptr;
   g->act_list = nullptr;
@@ -484,6 +486,9 @@ void free_bins(cd_graph* g) {
   g->hub_blist = nullptr;
   g->hub_mlist = nullptr;
   g->hub_lcnt = nullptr;
+  g->hub_log = nullptr;
+  g->hub_log_cnt = nullptr;
+  g->hub_log_cap = 0;
   g->nhubs = g->hub_slots = g->hub_items = g->hub_eval_items = 0;
 }
 
@@ -613,6 +618,14 @@ int build_bins(cd_graph* g) {
     if ((rc = dev_alloc_t(&g->hub_blist, g->hub_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_mlist, g->hub_items, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_lcnt, 2, s))) return rc;
+    {  // a round applies at most hub_arcs / HUB_LOG_DIV logged updates (random probes
+       // into the tables cost about as much as rebuilding the hubs); the hub of
+       // every update beyond that budget is rebuilt from its row instead
+      const int64_t hub_arcs = tab[nh] * 2 / 3;
+      g->hub_log_cap = std::max<int64_t>(1, hub_arcs / HUB_LOG_DIV);
+      if ((rc = dev_alloc_t(&g->hub_log, 2 * g->hub_log_cap, s))) return rc;
+      if ((rc = dev_alloc_t(&g->hub_log_cnt, 1, s))) return rc;
+    }
     CD_CHECK(cudaMemcpyAsync(g->hub_tab, tab.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_hub, item_hub.data(), item_hub.size() * 4, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_arc, item_arc.data(), item_arc.size() * 8, cudaMemcpyHostToDevice, s));

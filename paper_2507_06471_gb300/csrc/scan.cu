@@ -146,6 +146,9 @@ struct ScanCtx {
   const unsigned long long* small_cnt;
   int hub_upd;  // 0: neighbour moves do not update hub histograms (every hub is rebuilt next round)
   int64_t n_items, nhubs, n_ev_items;
+  unsigned long long* hub_log;  // hub-histogram updates of this round, applied after the scans (null: at once)
+  unsigned long long* hub_log_cnt;
+  int64_t hub_log_cap;
   // asynchronous mode: a committed move is applied at once through these
   int async_mode;
   int32_t* C_w;
@@ -423,8 +426,37 @@ __device__ __forceinline__ void hub_neighbour_moved(const ScanCtx& s, int32_t u,
   const uint32_t bits = __ldg(&s.hub_bits[u >> 5]);
   if (!((bits >> (u & 31)) & 1u)) return;
   const int32_t h = (int32_t)(__ldg(&s.hub_pref[u >> 5]) + __popc(bits & ((1u << (u & 31)) - 1u)));
+  if (s.hub_log) {
+    // appended as (h, A) and (c, w) words by the lanes that got here together;
+    // applied by k_hub_apply_log with every thread busy
+    cg::coalesced_group grp = cg::coalesced_threads();
+    unsigned long long pos = 0;
+    if (grp.thread_rank() == 0) pos = atomicAdd(s.hub_log_cnt, (unsigned long long)grp.size());
+    pos = grp.shfl(pos, 0) + grp.thread_rank();
+    if ((int64_t)pos < s.hub_log_cap) {
+      s.hub_log[2 * pos] = ((unsigned long long)(uint32_t)h << 32) | (uint32_t)A;
+      s.hub_log[2 * pos + 1] = ((unsigned long long)(uint32_t)c << 32) | (unsigned long long)(uint32_t)w;
+    } else {
+      hub_flag(s, h, HUB_REBUILD);  // log full: rebuild this hub from its row instead
+    }
+    return;
+  }
   hub_hist_add<false>(s, h, A, -w);
   hub_hist_add<false>(s, h, c, w);
+}
+
+// The round's logged hub-histogram updates, one thread per record.
+__global__ void __launch_bounds__(NT) k_hub_apply_log(ScanCtx s) {
+  const int64_t nrec = (int64_t)*(volatile unsigned long long*)s.hub_log_cnt;
+  const int64_t m = nrec < s.hub_log_cap ? nrec : s.hub_log_cap;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < m; i += stride) {
+    const unsigned long long a = s.hub_log[2 * i], b = s.hub_log[2 * i + 1];
+    const int32_t h = (int32_t)(a >> 32), A = (int32_t)(uint32_t)a, c = (int32_t)(b >> 32);
+    const int64_t w = (int64_t)(b & 0xffffffffull);
+    hub_hist_add<false>(s, h, A, -w);
+    hub_hist_add<false>(s, h, c, w);
+  }
 }
 
 // ------------------------------------------------------------------ tiles
@@ -1975,6 +2007,10 @@ ScanCtx static_ctx(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool 
   s.round_p = nullptr;
   s.hub_upd_p = nullptr;
   s.hub_upd = 1;
+  const bool log = g->nhubs > 0 && g->hub_log && !g->hub_wide && !o.async_mode;
+  s.hub_log = log ? g->hub_log : nullptr;
+  s.hub_log_cnt = log ? g->hub_log_cnt : nullptr;
+  s.hub_log_cap = log ? g->hub_log_cap : 0;
   return s;
 }
 
@@ -2076,6 +2112,7 @@ int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool p
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), cap));
       CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), cap));
       CD_CHECK(cudaMemsetAsync(cntB, 0, sizeof(unsigned long long), cap));
+      if (g->hub_log_cnt) CD_CHECK(cudaMemsetAsync(g->hub_log_cnt, 0, sizeof(unsigned long long), cap));
     }
     CD_LAUNCH(k_loop_begin<<<1, 1, 0, cap>>>(dl, n, louv ? HUB_SKIP_DIV : HUB_SKIP_DIV_LPA, nh > 0));
     if (compact) {
@@ -2109,6 +2146,7 @@ int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool p
       if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, cap>>>(s));
       else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, cap>>>(s));
       else CD_LAUNCH(k_hub_mark<WI64><<<gh, NT, 0, cap>>>(s));
+      if (s.hub_log) CD_LAUNCH(k_hub_apply_log<<<152 * 8, NT, 0, cap>>>(s));  // no records when not updating
       CD_LAUNCH(k_queue_all<<<grid_cap((nh + NT - 1) / NT), NT, 0, cap>>>(s, dl));
       CD_LAUNCH(k_flist_carry<<<grid_cap((nh + NT - 1) / NT), NT, 0, cap>>>(listB, cntB, listA, cntA));
     }
@@ -2227,6 +2265,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
+      if (g->hub_log_cnt) CD_CHECK(cudaMemsetAsync(g->hub_log_cnt, 0, sizeof(unsigned long long), st));
     }
     ScanCtx s = static_ctx(g, o, louv, use_s32, per_graph_stop);
     s.flag_cur = fcur;
@@ -2329,6 +2368,7 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
         if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, st>>>(s));
         else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, st>>>(s));
         else CD_LAUNCH(k_hub_mark<WI64><<<gh, NT, 0, st>>>(s));
+        if (s.hub_log && !skip_upd) CD_LAUNCH(k_hub_apply_log<<<152 * 8, NT, 0, st>>>(s));
       }
       CD_CHECK(cudaGetLastError());
     }
