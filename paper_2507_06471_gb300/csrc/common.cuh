@@ -138,6 +138,10 @@ struct cd_graph {
   uint32_t* sigma32 = nullptr;  // 32-bit copy for the gathers (allocated on first use)
   int32_t* csize = nullptr;
   uint32_t* flag[2] = {nullptr, nullptr};  // needCheck / tmpNeedCheck bitmaps (n bits each)
+  // streams for the scan kernels of different degree bins, which run concurrently
+  // when nothing they write is read by another (fork/join through events)
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
   int32_t* mv_v = nullptr;  // committed moves: vertex, new label, old label
   int32_t* mv_c = nullptr;
   int32_t* mv_a = nullptr;
@@ -190,7 +194,8 @@ struct KTimer {
   int k;
   double bytes;
   cudaEvent_t a = nullptr, b = nullptr;
-  KTimer(cd_graph* g_, int k_, double bytes_ = 0.0);
+  cudaStream_t st = nullptr;  // the stream the timed kernel runs on (g->stream if null)
+  KTimer(cd_graph* g_, int k_, double bytes_ = 0.0, cudaStream_t st_ = nullptr);
   ~KTimer();
 };
 void profile_reset(cd_graph* g);

@@ -59,17 +59,18 @@ void dev_free(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
-KTimer::KTimer(cd_graph* g_, int k_, double bytes_) : g(g_), k(k_), bytes(bytes_) {
+KTimer::KTimer(cd_graph* g_, int k_, double bytes_, cudaStream_t st_) : g(g_), k(k_), bytes(bytes_), st(st_) {
   if (g && g->timing) {
+    if (!st) st = g->stream;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    cudaEventRecord(a, g->stream);
+    cudaEventRecord(a, st);
   }
 }
 
 KTimer::~KTimer() {
   if (g && g->timing) {
-    cudaEventRecord(b, g->stream);
+    cudaEventRecord(b, st);
     g->pending.push_back({k, {a, b}});
     g->pending_bytes.push_back(bytes);
   }
@@ -733,6 +734,13 @@ int ensure_run_state(cd_graph* g) {
   if ((rc = dev_alloc_t(&g->mv_a, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->ctr, C_COUNT, s))) return rc;
   if (!g->h_ctr) CD_CHECK(cudaMallocHost(&g->h_ctr, C_COUNT * sizeof(int64_t)));
+  if (!g->fork_ev) {
+    CD_CHECK(cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming));
+    for (int i = 0; i < 3; ++i) {
+      CD_CHECK(cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking));
+      CD_CHECK(cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming));
+    }
+  }
   return CD_OK;
 }
 
@@ -952,6 +960,13 @@ int cd_graph_free(cd_graph* g) {
     cudaEventDestroy(p.second.second);
   }
   cudaStreamSynchronize(g->stream);
+  if (g->fork_ev) {
+    cudaEventDestroy(g->fork_ev);
+    for (int i = 0; i < 3; ++i) {
+      cudaStreamDestroy(g->aux[i]);
+      cudaEventDestroy(g->join_ev[i]);
+    }
+  }
   delete g;
   return CD_OK;
 }

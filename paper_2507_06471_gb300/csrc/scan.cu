@@ -1799,20 +1799,55 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
   return b;
 }
 
+// Scan kernels of different bins may run concurrently when none of them
+// writes what another reads: hub histograms are then only read during the
+// scans (their updates go to the log, applied after the join). fork() makes
+// the auxiliary streams wait for everything enqueued so far on g->stream;
+// join() makes g->stream wait for them.
+struct BinStreams {
+  cudaStream_t s[4];
+  bool on = false;
+};
+
+BinStreams fork_bins(cd_graph* g, bool concurrent) {
+  BinStreams b;
+  for (auto& x : b.s) x = g->stream;
+  if (!concurrent || !g->fork_ev) return b;
+  if (cudaEventRecord(g->fork_ev, g->stream) != cudaSuccess) return b;
+  for (int i = 0; i < 3; ++i) {
+    if (cudaStreamWaitEvent(g->aux[i], g->fork_ev, 0) != cudaSuccess) return b;
+    b.s[i + 1] = g->aux[i];
+  }
+  b.on = true;
+  return b;
+}
+
+int join_bins(cd_graph* g, const BinStreams& b) {
+  if (!b.on) return CD_OK;
+  for (int i = 0; i < 3; ++i) {
+    CD_CHECK(cudaEventRecord(g->join_ev[i], g->aux[i]));
+    CD_CHECK(cudaStreamWaitEvent(g->stream, g->join_ev[i], 0));
+  }
+  return CD_OK;
+}
+
 // Launch the first round from rows over every bin.
 template <bool LOUV, class W, bool NK>
 int launch_first_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, int>>& marks) {
-  cudaStream_t st = g->stream;
   auto cnt = [&](int b) { return g->bin_start[b + 1] - g->bin_start[b]; };
   auto lst = [&](int b) { return (const int32_t*)g->bin_list + g->bin_start[b]; };
   auto dcnt = [&](int b) { return (const unsigned long long*)g->full_cnt + b; };
   static const int kname[NBINS] = {K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP,
                                    K_SCAN_BLK128, K_SCAN_BLK512, K_HUB_EVAL};
+  // stream of each bin: hubs, the 512- and 128-thread groups, the warp bin, the tiles
+  static const int sidx[NBINS] = {0, 0, 0, 0, 3, 2, 2, 1};
+  const BinStreams bs = fork_bins(g, !s.async_mode);
   for (int b = NBINS - 1; b >= 0; --b) {
     const int64_t c = cnt(b);
     if (c == 0) continue;
+    const cudaStream_t st = bs.s[sidx[b]];
     {
-      KTimer t(g, kname[b]);
+      KTimer t(g, kname[b], 0.0, st);
       switch (b) {
         case B_T4: CD_LAUNCH((k_first_round<LOUV, W, NK, 4><<<grid_cap((c + 63) / 64), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
         case B_T8: CD_LAUNCH((k_first_round<LOUV, W, NK, 8><<<grid_cap((c + 31) / 32), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
@@ -1824,7 +1859,7 @@ int launch_first_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, in
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, b + FIRST_MARK});  // first-round bytes
   }
-  return CD_OK;
+  return join_bins(g, bs);
 }
 
 template <bool LOUV, bool NK>
@@ -1856,39 +1891,44 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
     if (g->timing) marks.push_back({g->pending.size() - 1, -1});
+  }
+  // the scans of the bins, concurrently when the hub histograms are only read
+  const BinStreams bs = fork_bins(g, !s.async_mode && (g->nhubs == 0 || s.hub_log != nullptr));
+  if (cnt(B_HUB) > 0) {
+    const cudaStream_t sh = bs.s[1];
     {
-      KTimer t(g, K_HUB_EVAL);
+      KTimer t(g, K_HUB_EVAL, 0.0, sh);
       if (g->n_small_hubs > 0)
         CD_LAUNCH(k_hub_eval_small<LOUV, NK><<<wave_grid(k_hub_eval_small<LOUV, NK>, NT, 0, (g->n_small_hubs + NW - 1) / NW),
-                                           NT, 0, st>>>(s));
-      CD_LAUNCH(k_hub_eval<LOUV, NK><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, st>>>(s));
+                                           NT, 0, sh>>>(s));
+      CD_LAUNCH(k_hub_eval<LOUV, NK><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, sh>>>(s));
     }
     if (g->timing) mark(B_HUB);
   }
   if (cnt(B_BLK4) > 0) {
     {
-      KTimer t(g, K_SCAN_BLK512);
+      KTimer t(g, K_SCAN_BLK512, 0.0, bs.s[2]);
       auto kern = k_scan_group<LOUV, W, V, 512, 512, BLK4_CAP_SLOTS, B_BLK4, false, NK>;
-      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk4_smem<V>(), cnt(B_BLK4)), 512, blk4_smem<V>(), st>>>(
+      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk4_smem<V>(), cnt(B_BLK4)), 512, blk4_smem<V>(), bs.s[2]>>>(
           s, lst(B_BLK4), dcnt(B_BLK4))));
     }
     if (g->timing) mark(B_BLK4);
   }
   if (cnt(B_BLK1) > 0) {
     {
-      KTimer t(g, K_SCAN_BLK128);
+      KTimer t(g, K_SCAN_BLK128, 0.0, bs.s[2]);
       auto kern = k_scan_group<LOUV, W, V, 128, 512, BLK1_CAP_SLOTS, B_BLK1, false, NK>;
-      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk1_smem<V>(), (cnt(B_BLK1) + 3) / 4), 512, blk1_smem<V>(), st>>>(
+      CD_LAUNCH((kern<<<wave_grid(kern, 512, blk1_smem<V>(), (cnt(B_BLK1) + 3) / 4), 512, blk1_smem<V>(), bs.s[2]>>>(
           s, lst(B_BLK1), dcnt(B_BLK1))));
     }
     if (g->timing) mark(B_BLK1);
   }
   if (cnt(B_WARP) > 0) {
     {
-      KTimer t(g, K_SCAN_WARP);
+      KTimer t(g, K_SCAN_WARP, 0.0, bs.s[3]);
       auto kern = k_scan_warp<LOUV, W, V, NK>;
       CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + 255) / 256), 256, warp_smem<V>(),
-                        st>>>(s, lst(B_WARP), dcnt(B_WARP))));
+                        bs.s[3]>>>(s, lst(B_WARP), dcnt(B_WARP))));
     }
     if (g->timing) mark(B_WARP);
   }
@@ -1929,7 +1969,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     if (g->timing) mark(B_T4);
   }
   CD_CHECK(cudaGetLastError());
-  return CD_OK;
+  return join_bins(g, bs);
 }
 
 template <bool LOUV, bool NK>
