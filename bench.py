@@ -84,6 +84,12 @@ def parse():
                     help="served: how many requests of the 20,000-request stream to run")
     ap.add_argument("--solo-sample", type=int, default=128,
                     help="batch workload: graphs timed one call per graph for the comparison")
+    ap.add_argument("--case", choices=["level1", "first-rounds"], default=None,
+                    help="profiling cases on R-MAT at --scale (default 23), run under ncu: 'level1' runs "
+                         "level 0 to convergence, aggregates, then local moving on the coarse graph with "
+                         "max_iter 3 and 4, the second inside cudaProfilerStart/Stop, and prints the "
+                         "algorithmic bytes of round 3 per kernel; 'first-rounds' runs LPA and local moving "
+                         "with max_iter 2 (round 1 builds every hub table)")
     return ap.parse_args()
 
 
@@ -717,9 +723,46 @@ def compact_many(line):
     return {k: line[k] for k in keep if k in line}
 
 
+def run_case(args):
+    """Small profiling cases (see --case); no timing line."""
+    import torch
+
+    import paper_2507_06471_gb300 as cd
+    import synth
+    g = synth.rmat(args.scale or 23, 16, seed=3, device="cuda")
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    G = cd.Graph(g.off, g.cols, None)
+    if args.case == "first-rounds":
+        G.lpa(max_iter=2)
+        G.local_move(max_iter=2)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "n": G.n, "arcs": G.nnz}))
+        return
+    lab, _, _ = G.local_move()
+    C, _ = G.aggregate(lab)
+    torch.cuda.synchronize()
+    prof = {}
+    for r in (3, 4):
+        if r == 4:
+            torch.cuda.profiler.start()
+        C.local_move(max_iter=r, timing=1)
+        torch.cuda.synchronize()
+        if r == 4:
+            torch.cuda.profiler.stop()
+        prof[r] = {x["name"]: x["alg_bytes"] for x in C.profile() if x["launches"]}
+    t = C.trace()[3]
+    print(json.dumps({"case": args.case, "n": C.n, "arcs": C.nnz,
+                      "round3": {"active": t["active"], "arcs": t["arcs"], "moved": t["moved"]},
+                      "alg_bytes_round3": {k: prof[4][k] - prof[3].get(k, 0.0) for k in prof[4]}}))
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
+    if args.case:
+        run_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

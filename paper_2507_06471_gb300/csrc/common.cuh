@@ -58,6 +58,8 @@ enum Ctr {
   C_HUB_BARCS = C_BIN0 + 3 * NBINS,  // arcs read by hub table builds this round
   C_HUB_BSLOTS,                      // table slots they (and the clears and compactions) wrote
   C_MARCS,                           // arcs of the vertices that moved this round
+  C_HUB_MARCS,                       // arcs of the hubs that moved this round
+  C_HUB_LOG,                         // hub-histogram updates logged this round
   C_COUNT
 };
 
@@ -125,7 +127,6 @@ struct cd_graph {
   int32_t* hub_cl = nullptr;               // 5 x nhubs: hubs rebuilt per build class
   unsigned long long* hub_ccnt = nullptr;  // 5: their counts
   unsigned long long* hub_log = nullptr;   // per round: hub-histogram updates (hub, old, new, w) to apply
-  unsigned long long* hub_log_cnt = nullptr;
   int64_t hub_log_cap = 0;
   int64_t max_degw = 0;            // largest deg_w (selects 32-bit table counters)
   bool cols_distinct = false;      // no row repeats a column (strictly increasing input rows, or coarse rows)

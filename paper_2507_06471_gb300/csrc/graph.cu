@@ -434,7 +434,7 @@ void free_arrays(cd_graph* g) {
                 g->hub_mv,       g->hub_rb,       g->hub_used,     g->hub_item_first,
                 g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
                 g->hub_blist,    g->hub_mlist,     g->hub_lcnt,     g->C,            g->sigma,        g->csize,
-                g->hub_log,      g->hub_log_cnt,
+                g->hub_log,
                 g->sigma32,
                 g->flag[0],      g->flag[1],       g->mv_v,         g->mv_c,         g->mv_a,
                 g->ctr,          g->status,        g->gid,          g->gbase,        g->gvol,
@@ -452,7 +452,7 @@ void free_bins(cd_graph* g) {
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
                 g->hub_rb,       g->hub_used,     g->hub_item_first, g->hub_blist,
                 g->hub_flist,    g->hub_fcnt,     g->hub_cl,       g->hub_ccnt,
-                g->hub_mlist,    g->hub_lcnt,     g->hub_log,      g->hub_log_cnt};
+                g->hub_mlist,    g->hub_lcnt,     g->hub_log};
   for (void* p : ps) dev_free(p, s);
   g->bin_list = nullptr;
   g->act_list = nullptr;
@@ -488,7 +488,6 @@ void free_bins(cd_graph* g) {
   g->hub_mlist = nullptr;
   g->hub_lcnt = nullptr;
   g->hub_log = nullptr;
-  g->hub_log_cnt = nullptr;
   g->hub_log_cap = 0;
   g->nhubs = g->hub_slots = g->hub_items = g->hub_eval_items = 0;
 }
@@ -625,7 +624,6 @@ int build_bins(cd_graph* g) {
       const int64_t hub_arcs = tab[nh] * 2 / 3;
       g->hub_log_cap = std::max<int64_t>(1, hub_arcs / HUB_LOG_DIV);
       if ((rc = dev_alloc_t(&g->hub_log, 2 * g->hub_log_cap, s))) return rc;
-      if ((rc = dev_alloc_t(&g->hub_log_cnt, 1, s))) return rc;
     }
     CD_CHECK(cudaMemcpyAsync(g->hub_tab, tab.data(), (nh + 1) * 8, cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaMemcpyAsync(g->hub_item_hub, item_hub.data(), item_hub.size() * 4, cudaMemcpyHostToDevice, s));

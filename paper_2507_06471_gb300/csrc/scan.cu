@@ -1192,6 +1192,7 @@ __device__ __forceinline__ void hub_decide(const ScanCtx& s, int32_t h, int32_t 
   n_def += def;
   if (target != cur && !def) {
     n_marcs += s.off[v + 1] - s.off[v];
+    atomicAdd(&s.ctr[C_HUB_MARCS], (unsigned long long)(s.off[v + 1] - s.off[v]));
     s.hub_mv[3 * h] = 1;
     s.hub_mv[3 * h + 1] = cur;
     s.hub_mv[3 * h + 2] = target;
@@ -2049,7 +2050,7 @@ ScanCtx static_ctx(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool 
   s.hub_upd = 1;
   const bool log = g->nhubs > 0 && g->hub_log && !g->hub_wide && !o.async_mode;
   s.hub_log = log ? g->hub_log : nullptr;
-  s.hub_log_cnt = log ? g->hub_log_cnt : nullptr;
+  s.hub_log_cnt = log ? (unsigned long long*)g->ctr + C_HUB_LOG : nullptr;  // cleared with the counters
   s.hub_log_cap = log ? g->hub_log_cap : 0;
   return s;
 }
@@ -2152,7 +2153,6 @@ int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool p
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), cap));
       CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), cap));
       CD_CHECK(cudaMemsetAsync(cntB, 0, sizeof(unsigned long long), cap));
-      if (g->hub_log_cnt) CD_CHECK(cudaMemsetAsync(g->hub_log_cnt, 0, sizeof(unsigned long long), cap));
     }
     CD_LAUNCH(k_loop_begin<<<1, 1, 0, cap>>>(dl, n, louv ? HUB_SKIP_DIV : HUB_SKIP_DIV_LPA, nh > 0));
     if (compact) {
@@ -2305,7 +2305,6 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
       CD_CHECK(cudaMemsetAsync(g->hub_lcnt, 0, 2 * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_ccnt, 0, HUB_NCLASS * sizeof(unsigned long long), st));
       CD_CHECK(cudaMemsetAsync(g->hub_fcnt + (r & 1), 0, sizeof(unsigned long long), st));
-      if (g->hub_log_cnt) CD_CHECK(cudaMemsetAsync(g->hub_log_cnt, 0, sizeof(unsigned long long), st));
     }
     ScanCtx s = static_ctx(g, o, louv, use_s32, per_graph_stop);
     s.flag_cur = fcur;
@@ -2403,7 +2402,9 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
           CD_LAUNCH(k_apply_state<false><<<gt, NT, 0, st>>>(s, s.ctr + C_MOVES, g->sigma, g->csize, g->C));
       }
       if (g->nhubs > 0) {
-        KTimer t(g, K_HUB_MARK);
+        // flags and logged updates of the moved hubs' arcs (column 4, flag 1), and every logged
+        // update (record 16, two slots read and written 32)
+        KTimer t(g, K_HUB_MARK, (double)h[C_HUB_MARCS] * 5 + (double)h[C_HUB_LOG] * (16 + 16 + 32));
         const unsigned gh = grid_cap(g->hub_items, 152 * 8);
         if (g->wkind == W_UNIT) CD_LAUNCH(k_hub_mark<WUnit><<<gh, NT, 0, st>>>(s));
         else if (g->wkind == W_I32) CD_LAUNCH(k_hub_mark<WI32><<<gh, NT, 0, st>>>(s));
