@@ -59,7 +59,11 @@ typedef struct cd_params {
   int32_t tie_keep_current; /* LPA tie rule: 1 keep the current label on a tie (default), 0 smallest */
   int32_t singleton_rule;   /* Louvain: 1 (default) singleton joins only a smaller-id singleton */
   int32_t use_frontier;     /* 1 (default): examine only flagged vertices; 0: all, every round */
-  int32_t timing;           /* 1: record CUDA-event times per round and per kernel (trace/profile) */
+  int32_t timing;           /* 0: none; 2: CUDA-event times per round (trace scan_ms/round_ms),
+                               kernels of different degree bins still run concurrently;
+                               1: per round and per kernel (trace and profile), the bins'
+                               kernels then run one after another so each event pair
+                               brackets one kernel alone */
   uint64_t sched_seed;      /* state of the deferral coin's SplitMix64 stream; default 0x5EED5EED */
   int32_t aggregation;      /* Louvain aggregation: 0 hash-combine per community (default), 1 radix sort
                                of all arcs; the coarse graphs have the same rows either way */
@@ -76,7 +80,7 @@ typedef struct cd_params {
                                host loop (building a graph per level costs more than the few round trips
                                of a small graph saves). 2: every run uses the device loop. 0: the host
                                loop everywhere (one read-back per round). Results are identical in every
-                               mode; timing = 1 always uses the host loop (it records per-round events) */
+                               mode; timing != 0 always uses the host loop (it records per-round events) */
 } cd_params;
 
 /* Per-round record of the last run on a graph (cd_trace_get). */
@@ -87,8 +91,8 @@ typedef struct cd_round_trace {
   int64_t arcs;     /* arcs scanned = sum of row lengths of examined vertices */
   int64_t moved;    /* vertices that changed label */
   int64_t deferred; /* vertices whose move was deferred by the coin */
-  float scan_ms;    /* device time of the scan kernels (timing = 1) */
-  float round_ms;   /* device time of the whole round (timing = 1) */
+  float scan_ms;    /* device time of the scan kernels (timing != 0) */
+  float round_ms;   /* device time of the whole round (timing != 0) */
   int64_t cands;    /* candidate pairs: distinct neighbour labels (own one included) summed over examined vertices */
   int64_t moved_arcs; /* arcs of the vertices that moved (their neighbours are flagged) */
 } cd_round_trace;
@@ -217,7 +221,9 @@ typedef struct cd_request_result {
 } cd_request_result;
 
 /* Start a server on the current device with parameters p (copied; timing is
- * ignored), 1 <= slots <= 64 workers, a device-memory budget in bytes (<= 0:
+ * ignored; device_loop = 1 keeps the host loop in the workers' packed calls,
+ * where concurrent graph instantiation costs more than it saves, and 2 still
+ * uses the device loop everywhere), 1 <= slots <= 64 workers, a device-memory budget in bytes (<= 0:
  * 80% of the free memory now), the packing limits small_n and batch_arcs
  * (0 turns packing off). Errors: CD_EINVAL, CD_ECUDA. */
 int cd_server_create(const cd_params* p, int32_t slots, int64_t mem_budget_bytes, int64_t small_n,

@@ -282,6 +282,7 @@ int aggregate(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_dev, 
   rc = graph_adopt(s, k, nseg, coff, ccols, cw, W_I64, &c, nullptr, nullptr, g);
   if (rc) return rc;
   c->timing = g->timing;
+  c->ktiming = g->ktiming;
   c->cols_distinct = true;  // one arc per pair of communities
   *coarse_out = c;
   return CD_OK;

@@ -139,10 +139,7 @@ struct cd_graph {
   uint32_t* sigma32 = nullptr;  // 32-bit copy for the gathers (allocated on first use)
   int32_t* csize = nullptr;
   uint32_t* flag[2] = {nullptr, nullptr};  // needCheck / tmpNeedCheck bitmaps (n bits each)
-  // streams for the scan kernels of different degree bins, which run concurrently
-  // when nothing they write is read by another (fork/join through events)
-  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
-  cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
+
   int32_t* mv_v = nullptr;  // committed moves: vertex, new label, old label
   int32_t* mv_c = nullptr;
   int32_t* mv_a = nullptr;
@@ -162,7 +159,8 @@ struct cd_graph {
 
   std::vector<cd_round_trace> trace;
   cd_kernel_profile prof[cd::K_COUNT] = {};
-  bool timing = false;
+  bool timing = false;   // per-round events (trace scan_ms/round_ms)
+  bool ktiming = false;  // per-kernel events (profile); the bins' kernels then run one after another
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;  // (kernel, events)
   std::vector<double> pending_bytes;
 };

@@ -60,7 +60,7 @@ void dev_free(void* p, cudaStream_t s) {
 }
 
 KTimer::KTimer(cd_graph* g_, int k_, double bytes_, cudaStream_t st_) : g(g_), k(k_), bytes(bytes_), st(st_) {
-  if (g && g->timing) {
+  if (g && g->ktiming) {
     if (!st) st = g->stream;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -69,7 +69,7 @@ KTimer::KTimer(cd_graph* g_, int k_, double bytes_, cudaStream_t st_) : g(g_), k
 }
 
 KTimer::~KTimer() {
-  if (g && g->timing) {
+  if (g && g->ktiming) {
     cudaEventRecord(b, st);
     g->pending.push_back({k, {a, b}});
     g->pending_bytes.push_back(bytes);
@@ -732,13 +732,6 @@ int ensure_run_state(cd_graph* g) {
   if ((rc = dev_alloc_t(&g->mv_a, g->n, s))) return rc;
   if ((rc = dev_alloc_t(&g->ctr, C_COUNT, s))) return rc;
   if (!g->h_ctr) CD_CHECK(cudaMallocHost(&g->h_ctr, C_COUNT * sizeof(int64_t)));
-  if (!g->fork_ev) {
-    CD_CHECK(cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming));
-    for (int i = 0; i < 3; ++i) {
-      CD_CHECK(cudaStreamCreateWithFlags(&g->aux[i], cudaStreamNonBlocking));
-      CD_CHECK(cudaEventCreateWithFlags(&g->join_ev[i], cudaEventDisableTiming));
-    }
-  }
   return CD_OK;
 }
 
@@ -958,13 +951,6 @@ int cd_graph_free(cd_graph* g) {
     cudaEventDestroy(p.second.second);
   }
   cudaStreamSynchronize(g->stream);
-  if (g->fork_ev) {
-    cudaEventDestroy(g->fork_ev);
-    for (int i = 0; i < 3; ++i) {
-      cudaStreamDestroy(g->aux[i]);
-      cudaEventDestroy(g->join_ev[i]);
-    }
-  }
   delete g;
   return CD_OK;
 }

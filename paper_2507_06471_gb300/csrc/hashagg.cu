@@ -540,6 +540,7 @@ int aggregate_hash(cd_graph* g, const int32_t* labels_dev, const int32_t* newid_
   rc = graph_adopt(s, k, nseg, coarse_off, ccols, cw, W_I64, &c, nullptr, nullptr, g);
   if (rc) return rc;
   c->timing = g->timing;
+  c->ktiming = g->ktiming;
   c->cols_distinct = true;  // one arc per pair of communities
   *coarse_out = c;
   return CD_OK;

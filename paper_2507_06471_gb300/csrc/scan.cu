@@ -793,15 +793,18 @@ __global__ void __launch_bounds__(NTB, GROUP == 32 ? ((LOUV || !W::unit) ? 4 : 5
   flush_counters(s, BIN, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
-// The warp bin (degrees 33..t_warp): a warp takes 32 listed vertices at a
-// time. Lane j loads vertex j's header; the warp then scans each active vertex
-// in turn (table inserts and evaluation as in k_scan_group) and lane j keeps
-// vertex j's best candidate. The 32 decisions, coins and move-list appends
-// then run in parallel, one lane per vertex, and the neighbours of the
-// committed moves are flagged (and their hub histograms updated) last.
+// The warp bin (degrees 33..t_warp): a warp takes vb (a power of two <= 32)
+// listed vertices at a time. Lane j < vb loads vertex j's header; the warp
+// then scans each active vertex in turn (table inserts and evaluation as in
+// k_scan_group) and lane j keeps vertex j's best candidate. The decisions,
+// coins and move-list appends then run in parallel, one lane per vertex, and
+// the neighbours of the committed moves are flagged (and their hub histograms
+// updated) last. vb = 32 on large bins; a small bin takes fewer vertices per
+// warp so that its warps still fill the GPU.
 template <bool LOUV, class W, class V, bool NK>
 __global__ void __launch_bounds__(256, (LOUV || !W::unit) ? 4 : 5)
-    k_scan_warp(ScanCtx s, const int32_t* __restrict__ list, const unsigned long long* __restrict__ count_p) {
+    k_scan_warp(ScanCtx s, const int32_t* __restrict__ list, const unsigned long long* __restrict__ count_p,
+                int vb) {
   typedef typename KeyOf<LOUV, NK>::T K;
   constexpr int CAP = WARP_CAP_SLOTS, WPB = 256 / 32;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -821,10 +824,11 @@ __global__ void __launch_bounds__(256, (LOUV || !W::unit) ? 4 : 5)
   const int64_t warp = ((int64_t)blockIdx.x * 256 + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * 256) >> 5;
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
-  for (int64_t base = warp * 32; base < count; base += nwarps * 32) {
+  for (int64_t base = warp * vb; base < count; base += nwarps * vb) {
     const int64_t i = base + lane;
-    const int32_t my_v = i < count ? list[i] : 0;
-    const VHdr h = load_hdr<LOUV>(s, my_v, i < count);
+    const bool in = lane < vb && i < count;
+    const int32_t my_v = in ? list[i] : 0;
+    const VHdr h = load_hdr<LOUV>(s, my_v, in);
     K my_bk = K(0);
     int32_t my_bc = NOCAND;
     bool my_hc = false;
@@ -1760,6 +1764,16 @@ unsigned wave_grid(KERN kernel, int nt, size_t smem, int64_t want) {
   return grid_cap(want, resident_ctas((const void*)kernel, nt, smem));
 }
 
+// Vertices per warp batch of k_scan_warp for a bin of cnt vertices: 32, or the
+// largest power of two that still gives every resident warp a batch.
+template <class KERN>
+int warp_batch(KERN kernel, size_t smem, int64_t cnt) {
+  const int64_t warps = (int64_t)resident_ctas((const void*)kernel, 256, smem) * 8;
+  int vb = 32;
+  while (vb > 1 && cnt < warps * vb) vb >>= 1;
+  return vb;
+}
+
 // Group-kernel configurations: (GROUP threads per vertex, CTA size, table slots).
 template <class V> constexpr size_t group_smem(int gpb, int cap, int ntb) {
   return (size_t)gpb * cap * (sizeof(V) + 4) + (size_t)(ntb / 32) * 32 * 8 + (size_t)gpb * cap * 2;
@@ -1810,14 +1824,36 @@ struct BinStreams {
   bool on = false;
 };
 
+// The auxiliary streams and their events belong to the calling host thread
+// (created on its first use), so handles cost no stream creation and the
+// server's worker threads never share them.
+struct AuxStreams {
+  cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+  bool ok = false;
+  AuxStreams() {
+    ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i)
+      ok = cudaStreamCreateWithFlags(&s[i], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+};
+
+AuxStreams& aux_streams() {
+  static thread_local AuxStreams a;
+  return a;
+}
+
 BinStreams fork_bins(cd_graph* g, bool concurrent) {
   BinStreams b;
   for (auto& x : b.s) x = g->stream;
-  if (!concurrent || !g->fork_ev) return b;
-  if (cudaEventRecord(g->fork_ev, g->stream) != cudaSuccess) return b;
+  if (!concurrent || g->ktiming) return b;  // per-kernel events need the kernels one after another
+  AuxStreams& a = aux_streams();
+  if (!a.ok || cudaEventRecord(a.fork, g->stream) != cudaSuccess) return b;
   for (int i = 0; i < 3; ++i) {
-    if (cudaStreamWaitEvent(g->aux[i], g->fork_ev, 0) != cudaSuccess) return b;
-    b.s[i + 1] = g->aux[i];
+    if (cudaStreamWaitEvent(a.s[i], a.fork, 0) != cudaSuccess) return b;
+    b.s[i + 1] = a.s[i];
   }
   b.on = true;
   return b;
@@ -1825,9 +1861,10 @@ BinStreams fork_bins(cd_graph* g, bool concurrent) {
 
 int join_bins(cd_graph* g, const BinStreams& b) {
   if (!b.on) return CD_OK;
+  AuxStreams& a = aux_streams();
   for (int i = 0; i < 3; ++i) {
-    CD_CHECK(cudaEventRecord(g->join_ev[i], g->aux[i]));
-    CD_CHECK(cudaStreamWaitEvent(g->stream, g->join_ev[i], 0));
+    CD_CHECK(cudaEventRecord(a.join[i], a.s[i]));
+    CD_CHECK(cudaStreamWaitEvent(g->stream, a.join[i], 0));
   }
   return CD_OK;
 }
@@ -1858,7 +1895,7 @@ int launch_first_round(cd_graph* g, ScanCtx& s, std::vector<std::pair<size_t, in
         default: CD_LAUNCH((k_first_round<LOUV, W, NK, 32><<<grid_cap((c + NW - 1) / NW), NT, 0, st>>>(s, lst(b), dcnt(b), b))); break;
       }
     }
-    if (g->timing) marks.push_back({g->pending.size() - 1, b + FIRST_MARK});  // first-round bytes
+    if (g->ktiming) marks.push_back({g->pending.size() - 1, b + FIRST_MARK});  // first-round bytes
   }
   return join_bins(g, bs);
 }
@@ -1891,7 +1928,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH((k_hub_build_cl<W, 4><<<304, HUB_NT, hub_cl_smem<4>(), st>>>(s)));
       CD_LAUNCH(k_hub_build<W, V><<<grid_cap(g->hub_items, 152 * 3), HUB_NT, hub_smem<V>(), st>>>(s));
     }
-    if (g->timing) marks.push_back({g->pending.size() - 1, -1});
+    if (g->ktiming) marks.push_back({g->pending.size() - 1, -1});
   }
   // the scans of the bins, concurrently when the hub histograms are only read
   const BinStreams bs = fork_bins(g, !s.async_mode && (g->nhubs == 0 || s.hub_log != nullptr));
@@ -1904,7 +1941,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
                                            NT, 0, sh>>>(s));
       CD_LAUNCH(k_hub_eval<LOUV, NK><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, sh>>>(s));
     }
-    if (g->timing) mark(B_HUB);
+    if (g->ktiming) mark(B_HUB);
   }
   if (cnt(B_BLK4) > 0) {
     {
@@ -1913,7 +1950,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH((kern<<<wave_grid(kern, 512, blk4_smem<V>(), cnt(B_BLK4)), 512, blk4_smem<V>(), bs.s[2]>>>(
           s, lst(B_BLK4), dcnt(B_BLK4))));
     }
-    if (g->timing) mark(B_BLK4);
+    if (g->ktiming) mark(B_BLK4);
   }
   if (cnt(B_BLK1) > 0) {
     {
@@ -1922,16 +1959,17 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH((kern<<<wave_grid(kern, 512, blk1_smem<V>(), (cnt(B_BLK1) + 3) / 4), 512, blk1_smem<V>(), bs.s[2]>>>(
           s, lst(B_BLK1), dcnt(B_BLK1))));
     }
-    if (g->timing) mark(B_BLK1);
+    if (g->ktiming) mark(B_BLK1);
   }
   if (cnt(B_WARP) > 0) {
     {
       KTimer t(g, K_SCAN_WARP, 0.0, bs.s[3]);
       auto kern = k_scan_warp<LOUV, W, V, NK>;
-      CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + 255) / 256), 256, warp_smem<V>(),
-                        bs.s[3]>>>(s, lst(B_WARP), dcnt(B_WARP))));
+      const int vb = warp_batch(kern, warp_smem<V>(), cnt(B_WARP));
+      CD_LAUNCH((kern<<<wave_grid(kern, 256, warp_smem<V>(), (cnt(B_WARP) + 8 * vb - 1) / (8 * vb)), 256,
+                        warp_smem<V>(), bs.s[3]>>>(s, lst(B_WARP), dcnt(B_WARP), vb)));
     }
-    if (g->timing) mark(B_WARP);
+    if (g->ktiming) mark(B_WARP);
   }
   if (cnt(B_T32) > 0) {
     {
@@ -1940,7 +1978,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T32) + NW - 1) / (NW)), NT, 0, st>>>(
           s, lst(B_T32), dcnt(B_T32), B_T32));
     }
-    if (g->timing) mark(B_T32);
+    if (g->ktiming) mark(B_T32);
   }
   if (cnt(B_T16) > 0) {
     {
@@ -1949,7 +1987,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T16) + 2 * NW - 1) / (2 * NW)), NT, 0, st>>>(
           s, lst(B_T16), dcnt(B_T16), B_T16));
     }
-    if (g->timing) mark(B_T16);
+    if (g->ktiming) mark(B_T16);
   }
   if (cnt(B_T8) > 0) {
     {
@@ -1958,7 +1996,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T8) + 4 * NW - 1) / (4 * NW)), NT, 0, st>>>(
           s, lst(B_T8), dcnt(B_T8), B_T8));
     }
-    if (g->timing) mark(B_T8);
+    if (g->ktiming) mark(B_T8);
   }
   if (cnt(B_T4) > 0) {
     {
@@ -1967,7 +2005,7 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
       CD_LAUNCH(kern<<<wave_grid(kern, NT, 0, (cnt(B_T4) + 8 * NW - 1) / (8 * NW)), NT, 0, st>>>(
           s, lst(B_T4), dcnt(B_T4), B_T4));
     }
-    if (g->timing) mark(B_T4);
+    if (g->ktiming) mark(B_T4);
   }
   CD_CHECK(cudaGetLastError());
   return join_bins(g, bs);
@@ -2539,6 +2577,7 @@ int begin_run(cd_graph* g, const cd_params* p) {
       p->max_levels > 32767)
     return CD_EINVAL;
   g->timing = p->timing != 0;
+  g->ktiming = p->timing == 1;
   g->trace.clear();
   profile_reset(g);
   return CD_OK;
@@ -2600,8 +2639,8 @@ int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp
   CD_CHECK(cudaEventCreate(&b));
   float best = -1.f;
   int bw = g->t_warp, bh = g->t_hub;
-  const bool timing = g->timing;
-  g->timing = false;
+  const bool timing = g->timing, ktiming = g->ktiming;
+  g->timing = g->ktiming = false;
   for (int i = 0; i < 3 && !rc; ++i)
     for (int j = 0; j < 4 && !rc; ++j) {
       if (th[j] < tw[i]) continue;
@@ -2623,6 +2662,7 @@ int cd_autotune(cd_graph* g, const cd_params* p, int32_t rounds, int32_t* t_warp
       }
     }
   g->timing = timing;
+  g->ktiming = ktiming;
   g->trace.clear();
   cudaEventDestroy(a);
   cudaEventDestroy(b);

@@ -217,6 +217,10 @@ int cd_server_create(const cd_params* p, int32_t slots, int64_t mem_budget_bytes
   cd_server* s = new cd_server();
   s->params = *p;
   s->params.timing = 0;
+  // device_loop 1 means "batched calls": the workers' packed calls keep the
+  // host loop, since several workers capturing and instantiating round graphs
+  // at once cost more than the round trips they save (2 still forces it)
+  if (s->params.device_loop == 1) s->params.device_loop = 0;
   cudaGetDevice(&s->device);
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
