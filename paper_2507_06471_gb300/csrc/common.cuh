@@ -88,16 +88,15 @@ struct cd_graph {
   int64_t bin_start[cd::NBINS + 1] = {};  // host copy of the bin offsets
   // frontier: the active vertices of a round, bin b at act_list + bin_start[b]
   int32_t* act_list = nullptr;
-  unsigned long long* act_cnt = nullptr;   // NBINS+2: active per bin, large-hub items, small hubs
+  unsigned long long* act_cnt = nullptr;   // NBINS+2: active per bin (hub bin: hub numbers), then the
+                                           // evaluate items and small hubs routed this round
   unsigned long long* full_cnt = nullptr;  // NBINS+2: the same for every listed vertex
-  int32_t* act_ev = nullptr;               // evaluate items of the active large hubs
-  int32_t* act_small = nullptr;            // active small hubs
-  int32_t* hub_big_items = nullptr;        // every evaluate item of a large hub
-  int32_t* hub_small = nullptr;            // every small hub
-  int64_t n_small_hubs = 0, n_big_items = 0;
+  int32_t* act_ev = nullptr;               // evaluate items of the examined hubs with large tables in use
+  int32_t* act_small = nullptr;            // examined hubs with small tables in use (one warp each)
   // hubs (degree > BLOCK_MAX): one persistent label histogram per hub, kept in
   // step with the labels by the moves of its neighbours: an open-addressing
-  // table of cap_h = 1.5 deg + 64 slots in [hub_tab[h], hub_tab[h+1]). A slot
+  // table allocated cap_h = 1.5 deg + 64 slots in [hub_tab[h], hub_tab[h+1]),
+  // of which the first hub_cc[h] are in use (a compaction shrinks it). A slot
   // is one word (label << 32 | count) when every deg_w < 2^32 ("packed"),
   // otherwise two words (label, count).
   int64_t nhubs = 0, hub_slots = 0, hub_items = 0, hub_eval_items = 0;
@@ -105,6 +104,8 @@ struct cd_graph {
   uint32_t* hub_pref = nullptr;        // per 32-vertex word: hubs with smaller vertex ids (hub number = rank)
   uint32_t* hub_bits = nullptr;            // (n+31)/32: bit v set iff v is a hub
   int64_t* hub_tab = nullptr;              // nhubs+1
+  int64_t* hub_cc = nullptr;               // nhubs: slots in use, [0, hub_cc) of the allocation (rest empty)
+  int32_t* hub_live = nullptr;             // nhubs: live entries counted by the evaluate items of a round
   unsigned long long* hub_slot = nullptr;  // hub_slots words (x2 when wide)
   int32_t* hub_item_hub = nullptr;         // per build/mark item (HUB_CHUNK arcs): hub
   int64_t* hub_item_arc = nullptr;         // per build/mark item: first arc

@@ -427,7 +427,7 @@ void free_arrays(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->off,          g->cols,          g->w,            g->degw,         g->bin_list,
                 g->act_list,     g->act_cnt,       g->full_cnt,     g->act_ev,       g->act_small,
-                g->hub_big_items, g->hub_small,
+                g->hub_cc,       g->hub_live,
                 g->hub_pref,      g->hub_bits,      g->hub_tab,       g->hub_slot,
                 g->hub_item_hub,  g->hub_item_arc, g->hub_ev_hub,   g->hub_ev_slot,
                 g->hub_ev_first, g->hub_part,      g->hub_cur,      g->hub_hascur,   g->hub_done,
@@ -446,7 +446,7 @@ void free_arrays(cd_graph* g) {
 void free_bins(cd_graph* g) {
   cudaStream_t s = g->stream;
   void* ps[] = {g->bin_list,     g->act_list,    g->act_cnt,      g->full_cnt,  g->act_ev,
-                g->act_small,    g->hub_big_items, g->hub_small,
+                g->act_small,    g->hub_cc,       g->hub_live,
                 g->hub_pref,      g->hub_bits,     g->hub_tab,   g->hub_slot,
                 g->hub_item_hub, g->hub_item_arc, g->hub_ev_hub,  g->hub_ev_slot, g->hub_ev_first,
                 g->hub_part,     g->hub_cur,     g->hub_hascur,   g->hub_done,  g->hub_mv,
@@ -460,9 +460,8 @@ void free_bins(cd_graph* g) {
   g->full_cnt = nullptr;
   g->act_ev = nullptr;
   g->act_small = nullptr;
-  g->hub_big_items = nullptr;
-  g->hub_small = nullptr;
-  g->n_small_hubs = g->n_big_items = 0;
+  g->hub_cc = nullptr;
+  g->hub_live = nullptr;
   g->hub_pref = nullptr;
   g->hub_bits = nullptr;
   g->hub_tab = nullptr;
@@ -560,7 +559,8 @@ int build_bins(cd_graph* g) {
     CD_CHECK(cudaStreamSynchronize(s));
     dev_free(d_rows, s);
     std::vector<int64_t> tab(nh + 1, 0), item_arc, ev_first(nh + 1, 0), ev_slot, item_first(nh + 1, 0);
-    std::vector<int32_t> item_hub, ev_hub, small, big_items;
+    std::vector<int32_t> item_hub, ev_hub;
+    std::vector<int64_t> cc(nh);
     for (int64_t h = 0; h < nh; ++h) {
       int64_t beg = rows[2 * h], deg = rows[2 * h + 1] - beg;
       int64_t cap = deg + deg / 2 + 64;  // live labels <= deg; the rest absorbs labels that come and go
@@ -571,9 +571,7 @@ int build_bins(cd_graph* g) {
         item_arc.push_back(beg + a);
       }
       ev_first[h] = (int64_t)ev_hub.size();
-      if (cap <= HUB_SMALL) small.push_back((int32_t)h);
       for (int64_t e = 0; e < cap; e += HUB_SLICE) {
-        if (cap > HUB_SMALL) big_items.push_back((int32_t)ev_hub.size());
         ev_hub.push_back((int32_t)h);
         ev_slot.push_back(e);
       }
@@ -584,15 +582,12 @@ int build_bins(cd_graph* g) {
     g->hub_items = (int64_t)item_hub.size();
     g->hub_eval_items = (int64_t)ev_hub.size();
     if ((rc = dev_alloc_t(&g->act_ev, g->hub_eval_items, s))) return rc;
-    g->n_small_hubs = (int64_t)small.size();
-    g->n_big_items = (int64_t)big_items.size();
-    if ((rc = dev_alloc_t(&g->act_small, g->n_small_hubs, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_small, g->n_small_hubs, s))) return rc;
-    if ((rc = dev_alloc_t(&g->hub_big_items, g->n_big_items, s))) return rc;
-    if (!small.empty())
-      CD_CHECK(cudaMemcpyAsync(g->hub_small, small.data(), small.size() * 4, cudaMemcpyHostToDevice, s));
-    if (!big_items.empty())
-      CD_CHECK(cudaMemcpyAsync(g->hub_big_items, big_items.data(), big_items.size() * 4, cudaMemcpyHostToDevice, s));
+    if ((rc = dev_alloc_t(&g->act_small, nh, s))) return rc;  // any hub whose table in use is small
+    if ((rc = dev_alloc_t(&g->hub_cc, nh, s))) return rc;
+    if ((rc = dev_alloc_t(&g->hub_live, nh, s))) return rc;
+    for (int64_t h = 0; h < nh; ++h) cc[h] = tab[h + 1] - tab[h];  // every table starts at its allocation
+    CD_CHECK(cudaMemcpyAsync(g->hub_cc, cc.data(), nh * 8, cudaMemcpyHostToDevice, s));
+    CD_CHECK(cudaMemsetAsync(g->hub_live, 0, nh * 4, s));
     if ((rc = dev_alloc_t(&g->hub_pref, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_bits, (g->n + 31) / 32, s))) return rc;
     if ((rc = dev_alloc_t(&g->hub_tab, nh + 1, s))) return rc;
@@ -650,8 +645,7 @@ int build_bins(cd_graph* g) {
   {
     unsigned long long full[NBINS + 2];
     for (int b = 0; b < NBINS; ++b) full[b] = (unsigned long long)(g->bin_start[b + 1] - g->bin_start[b]);
-    full[NBINS] = (unsigned long long)g->n_big_items;
-    full[NBINS + 1] = (unsigned long long)g->n_small_hubs;
+    full[NBINS] = full[NBINS + 1] = 0;  // hub evaluate work is routed per round
     CD_CHECK(cudaMemcpyAsync(g->full_cnt, full, sizeof(full), cudaMemcpyHostToDevice, s));
     CD_CHECK(cudaStreamSynchronize(s));  // `full` lives on this stack frame
   }

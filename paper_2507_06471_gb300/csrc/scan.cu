@@ -116,6 +116,8 @@ struct ScanCtx {
   const uint32_t* hub_pref;
   const uint32_t* hub_bits;
   const int64_t* hub_tab;
+  int64_t* hub_cc;                   // per hub: slots in use, [0, hub_cc) of its allocation (the rest empty)
+  int32_t* hub_live;                 // per hub: live entries counted by this round's evaluate items
   unsigned long long* hub_slot;
   int hub_wide;
   const int32_t* hub_item_hub;
@@ -144,6 +146,8 @@ struct ScanCtx {
   const unsigned long long* ev_cnt;  // their number
   const int32_t* small_list;         // small hubs (one warp each) to evaluate this round
   const unsigned long long* small_cnt;
+  const int32_t* hub_act;            // hubs examined this round (null: every hub)
+  const unsigned long long* hub_act_cnt;
   int hub_upd;  // 0: neighbour moves do not update hub histograms (every hub is rebuilt next round)
   int64_t n_items, nhubs, n_ev_items;
   unsigned long long* hub_log;  // hub-histogram updates of this round, applied after the scans (null: at once)
@@ -353,7 +357,7 @@ template <bool BUILD>
 __device__ __forceinline__ void hub_hist_add(const ScanCtx& s, int32_t h, int32_t label, int64_t w) {
   if (!BUILD && s.hub_rb[h] == HUB_REBUILD) return;
   const int64_t base = s.hub_tab[h];
-  const int64_t cap = s.hub_tab[h + 1] - base;
+  const int64_t cap = s.hub_cc[h];
   const int64_t lim = BUILD ? cap : (cap < HUB_PROBE_MAX ? cap : HUB_PROBE_MAX);
   int64_t slot = hub_home(label, cap);
   bool claimed = false;
@@ -929,15 +933,29 @@ template <> struct HubClass<2> { static constexpr int C = 2, NT = 512, SLOTS = H
 template <> struct HubClass<3> { static constexpr int C = 4, NT = 512, SLOTS = HUB_CL_SLOTS; };
 template <> struct HubClass<4> { static constexpr int C = 8, NT = 512, SLOTS = HUB_CL_SLOTS; };
 template <int CI> constexpr size_t hub_cl_smem() { return (size_t)HubClass<CI>::SLOTS * 8; }
-constexpr int HUB_PREP_SLOTS = 12288;  // largest table compacted in shared memory
+constexpr int HUB_PREP_SLOTS = 12288;  // shared-memory slots of a compaction (live list + new table)
 constexpr size_t HUB_PREP_SMEM = (size_t)HUB_PREP_SLOTS * 8;
 
+// A hub's table in use is [0, cc) of its allocation of A = 1.5 deg + 64
+// slots; the slots past cc are empty. A rebuild from the row takes all of A
+// (the number of distinct labels is not known before it). When an evaluation
+// finds at most a quarter of the slots in use holding live entries, the hub
+// is queued for compaction, which rehashes them into 2 live + 64 slots. Late
+// in a level most hubs' neighbours sit in few communities, so an evaluation
+// then reads a few hundred slots instead of 1.5 deg.
+constexpr int64_t HUB_SHRINK_MIN = 512;  // tables in use this small are left as they are
+__device__ __forceinline__ void hub_maybe_shrink(const ScanCtx& s, int32_t h, int64_t cc, int64_t live) {
+  if (!s.hub_wide && cc > HUB_SHRINK_MIN && live * 4 < cc && 3 * live + 64 <= HUB_PREP_SLOTS && s.hub_rb[h] == 0)
+    hub_flag(s, h, HUB_COMPACT);
+}
+
 // Start of a round, a CTA per hub flagged in the previous round (every hub in
-// round 0). COMPACT (packed slots, table of at most HUB_PREP_SLOTS): the live
-// entries (count > 0) are rehashed into a fresh layout in shared memory, which
-// is written back with coalesced stores. REBUILD or a larger table: the table
-// is cleared (unless a single build item will overwrite it whole) and the
-// hub's build items are queued.
+// round 0). COMPACT (packed slots): the live entries (count > 0) are listed at
+// the top of shared memory and rehashed below them into a table of 2 live + 64
+// slots (at most the allocation), which is written back with coalesced stores
+// (the slots it no longer uses are cleared). REBUILD, or too many live entries
+// for shared memory: the table goes back to its whole allocation, is cleared
+// (unless a cluster build overwrites it whole) and the hub's build is queued.
 __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* T = (unsigned long long*)smem;
@@ -946,35 +964,49 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
   const int64_t nf = (int64_t)*(volatile const unsigned long long*)s.hub_fcnt_r;
   for (int64_t q = blockIdx.x; q < nf; q += gridDim.x) {
     const int32_t h = s.hub_flist_r[q];
-    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;
+    const int64_t base = s.hub_tab[h], cap = s.hub_tab[h + 1] - base;  // the allocation
+    const int64_t cc = s.hub_cc[h];                                     // slots in use
     const int64_t i0 = s.hub_item_first[h], ni = s.hub_item_first[h + 1] - i0;
-    if (s.hub_rb[h] == HUB_COMPACT && !s.hub_wide && cap <= HUB_PREP_SLOTS) {  // uniform in the CTA
-      for (int64_t i = threadIdx.x; i < cap; i += NT) T[i] = SLOT_EMPTY;
+    if (s.hub_rb[h] == HUB_COMPACT && !s.hub_wide) {  // uniform in the CTA
       if (threadIdx.x == 0) n_live = 0;
       __syncthreads();
-      for (int64_t i = threadIdx.x; i < cap; i += NT) {
+      for (int64_t i = threadIdx.x; i < cc; i += NT) {
         const unsigned long long x = s.hub_slot[base + i];
         if (x == SLOT_EMPTY || (x & 0xffffffffull) == 0) continue;
-        int64_t slot = hub_home((int32_t)(x >> 32), cap);
-        for (int64_t probe = 0; probe < cap; ++probe) {  // fewer live entries than slots: always ends
-          if (atomicCAS(&T[slot], SLOT_EMPTY, x) == SLOT_EMPTY) break;
-          slot = slot + 1 == cap ? 0 : slot + 1;
+        const int j = atomicAdd(&n_live, 1);
+        if (j < HUB_PREP_SLOTS) T[HUB_PREP_SLOTS - 1 - j] = x;  // the live list grows down from the top
+      }
+      __syncthreads();
+      const int64_t nl = n_live;
+      const int64_t nc = 2 * nl + 64 < cap ? 2 * nl + 64 : cap;
+      if (nc + nl <= HUB_PREP_SLOTS) {  // the new table [0, nc) lies below the list
+        for (int64_t i = threadIdx.x; i < nc; i += NT) T[i] = SLOT_EMPTY;
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < nl; j += NT) {
+          const unsigned long long x = T[HUB_PREP_SLOTS - 1 - j];
+          int64_t slot = hub_home((int32_t)(x >> 32), nc);
+          for (int64_t probe = 0; probe < nc; ++probe) {  // nl < nc: always ends
+            if (atomicCAS(&T[slot], SLOT_EMPTY, x) == SLOT_EMPTY) break;
+            slot = slot + 1 == nc ? 0 : slot + 1;
+          }
         }
-        atomicAdd(&n_live, 1);
+        __syncthreads();
+        for (int64_t i = threadIdx.x; i < nc; i += NT) s.hub_slot[base + i] = T[i];
+        for (int64_t i = nc + threadIdx.x; i < cc; i += NT) s.hub_slot[base + i] = SLOT_EMPTY;
+        if (threadIdx.x == 0) {
+          s.hub_cc[h] = nc;
+          s.hub_used[h] = (int32_t)nl;
+          s.hub_rb[h] = 0;
+          atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)(2 * cc));  // read and written
+        }
+        __syncthreads();
+        continue;
       }
-      __syncthreads();
-      for (int64_t i = threadIdx.x; i < cap; i += NT) s.hub_slot[base + i] = T[i];
-      if (threadIdx.x == 0) {
-        s.hub_used[h] = n_live;
-        s.hub_rb[h] = 0;
-        atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)(2 * cap));  // read and written
-      }
-      __syncthreads();
-      continue;
     }
     if (!s.hub_wide && hub_class(cap) >= 0) {  // one CTA or a cluster builds it and writes the whole table
       if (threadIdx.x == 0) {
         const int c = hub_class(cap);
+        s.hub_cc[h] = cap;
         s.hub_used[h] = 0;
         s.hub_rb[h] = HUB_REBUILD;  // cleared by the cluster once built
         s.hub_cl[(int64_t)c * s.nhubs + (int64_t)atomicAdd(&s.hub_ccnt[c], 1ull)] = h;
@@ -982,9 +1014,11 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       __syncthreads();
       continue;
     }
-    {  // giant or two-word hubs: cleared here, built by items with global inserts
-      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)cap);
-      for (int64_t i = threadIdx.x; i < cap; i += NT) {
+    {  // giant or two-word hubs: cleared here (the slots past cc are empty already),
+       // built by items with global inserts
+      const int64_t clr = s.hub_wide ? cap : cc;
+      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)clr);
+      for (int64_t i = threadIdx.x; i < clr; i += NT) {
         if (!s.hub_wide) {
           s.hub_slot[base + i] = SLOT_EMPTY;
         } else {
@@ -994,6 +1028,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
       }
     }
     if (threadIdx.x == 0) {
+      s.hub_cc[h] = cap;
       s.hub_used[h] = 0;
       s.hub_rb[h] = HUB_REBUILD;  // cleared once built (start of the evaluate kernel)
       pos = atomicAdd(&s.hub_lcnt[0], (unsigned long long)ni);
@@ -1226,11 +1261,12 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
     const int64_t dv = LOUV ? s.degw[v] : 0;
     const int64_t volv = LOUV ? vol_of(s, v) : 0;
     const int64_t base = s.hub_tab[h];
-    const int64_t cap = s.hub_tab[h + 1] - base;
+    const int64_t cap = s.hub_cc[h];
     K bk = K(0);
     int32_t bc = NOCAND;
     bool hc = false;
     int64_t kc = 0;
+    unsigned nl = 0;  // live entries seen by this lane
     constexpr int U = 4;  // slots per lane per batch, then their gathers
     for (int64_t e = lane; e < cap; e += U * 32) {
       int32_t c[U];
@@ -1248,6 +1284,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
       for (int j = 0; j < U; ++j) {
         if (c[j] < 0 || k[j] == 0) continue;
         ++n_cand;
+        ++nl;
         if (c[j] == cur) {
           hc = true;
           kc = k[j];
@@ -1263,21 +1300,28 @@ __global__ void __launch_bounds__(NT) k_hub_eval_small(ScanCtx s) {
     reduce_best(bk, bc, 32);
     const unsigned hm = __ballot_sync(FULL, hc);
     if (hm) kc = __shfl_sync(FULL, kc, __ffs(hm) - 1);
-    if (lane == 0) hub_decide<LOUV, NK>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def, n_marcs);
+    nl = __reduce_add_sync(FULL, nl);
+    if (lane == 0) {
+      hub_decide<LOUV, NK>(s, h, v, cur, bk, bc, hm != 0, kc, volv, n_act, n_arcs, n_def, n_marcs);
+      hub_maybe_shrink(s, h, cap, nl);
+    }
   }
   flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def, n_marcs);
 }
 
-// Every item scans HUB_SLICE histogram entries of one active hub; the last
-// item of a hub to finish combines the partial bests and decides. Entries
-// with weight 0 (labels that left the neighbourhood) are not candidates.
+// Every item scans HUB_SLICE histogram entries of one active hub (the hub's
+// first ceil(cc / HUB_SLICE) items are listed); the last item of a hub to
+// finish combines the partial bests and decides. Entries with weight 0
+// (labels that left the neighbourhood) are not candidates.
 template <bool LOUV, bool NK>
 __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
   typedef typename KeyOf<LOUV, NK>::T K;
   __shared__ K red_k[NW];
   __shared__ int32_t red_c[NW];
   __shared__ int s_last;
+  __shared__ unsigned s_live;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_live = 0;
   {
     const int64_t nb = (int64_t)*(volatile unsigned long long*)&s.hub_lcnt[0];
     for (int64_t q = (int64_t)blockIdx.x * NT + threadIdx.x; q < nb; q += (int64_t)gridDim.x * NT) {
@@ -1286,6 +1330,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       if (s.hub_item_first[h] == it) s.hub_rb[h] = 0;
     }
   }
+  __syncthreads();
   int64_t n_act = 0, n_arcs = 0, n_cand = 0, n_def = 0, n_marcs = 0;
   const int64_t n_ev = (int64_t)*s.ev_cnt;
   for (int64_t q = blockIdx.x; q < n_ev; q += gridDim.x) {
@@ -1297,11 +1342,12 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
     const int64_t dv = LOUV ? s.degw[v] : 0;
     const int64_t volv = LOUV ? vol_of(s, v) : 0;
     const int64_t base = s.hub_tab[h];
-    const int64_t cap = s.hub_tab[h + 1] - base;
+    const int64_t cap = s.hub_cc[h];
     const int64_t e0 = s.hub_ev_slot[it];
     const int64_t e1 = e0 + HUB_SLICE < cap ? e0 + HUB_SLICE : cap;
     K bk = K(0);
     int32_t bc = NOCAND;
+    unsigned nl = 0;
     constexpr int HB = 6;  // slots per thread per batch: all loads, then all gathers, in flight together
     for (int64_t e = e0 + threadIdx.x; e < e1; e += HB * NT) {
       int32_t c[HB];
@@ -1319,6 +1365,7 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       for (int j = 0; j < HB; ++j) {
         if (c[j] < 0 || k[j] == 0) continue;  // unused entry, or a label that left
         ++n_cand;
+        ++nl;
         if (c[j] == cur) {
           s.hub_cur[h] = k[j];
           s.hub_hascur[h] = 1;
@@ -1332,9 +1379,11 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       }
     }
     reduce_best(bk, bc, 32);
+    nl = __reduce_add_sync(FULL, nl);
     if (lane == 0) {
       red_k[wid] = bk;
       red_c[wid] = bc;
+      if (nl) atomicAdd(&s_live, nl);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -1347,8 +1396,9 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       s.hub_part[3 * it] = (int64_t)(kk >> 64);
       s.hub_part[3 * it + 1] = (int64_t)(uint64_t)kk;
       s.hub_part[3 * it + 2] = bc;
+      if (s_live) atomicAdd(&s.hub_live[h], (int)s_live);
       __threadfence();
-      const int64_t nparts = s.hub_ev_first[h + 1] - s.hub_ev_first[h];
+      const int64_t nparts = (cap + HUB_SLICE - 1) / HUB_SLICE;
       s_last = atomicAdd(&s.hub_done[h], 1) == (int)(nparts - 1);
     }
     __syncthreads();
@@ -1357,7 +1407,8 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       const volatile int64_t* part = s.hub_part;
       K fk = K(0);
       int32_t fc = NOCAND;
-      for (int64_t p = s.hub_ev_first[h]; p < s.hub_ev_first[h + 1]; ++p) {
+      const int64_t p0 = s.hub_ev_first[h], p1 = p0 + (cap + HUB_SLICE - 1) / HUB_SLICE;
+      for (int64_t p = p0; p < p1; ++p) {
         const i128 pk = (i128)(((unsigned __int128)(uint64_t)part[3 * p] << 64) | (uint64_t)part[3 * p + 1]);
         const int32_t pc = (int32_t)part[3 * p + 2];
         if (better((K)pk, pc, fk, fc)) {
@@ -1368,10 +1419,13 @@ __global__ void __launch_bounds__(NT) k_hub_eval(ScanCtx s) {
       const bool hc = *((volatile int32_t*)&s.hub_hascur[h]) != 0;
       const int64_t kc = hc ? *((volatile int64_t*)&s.hub_cur[h]) : 0;
       hub_decide<LOUV, NK>(s, h, v, cur, fk, fc, hc, kc, volv, n_act, n_arcs, n_def, n_marcs);
+      hub_maybe_shrink(s, h, cap, *(volatile int32_t*)&s.hub_live[h]);
+      s.hub_live[h] = 0;
       s.hub_done[h] = 0;
       s.hub_cur[h] = 0;
       s.hub_hascur[h] = 0;
     }
+    if (threadIdx.x == 0) s_live = 0;
     __syncthreads();
   }
   flush_counters(s, B_HUB, n_act, n_arcs, n_cand, n_def, n_marcs);
@@ -1567,12 +1621,12 @@ struct BinBounds {
 };
 
 // The active vertices of a round into per-bin lists (bin b at act + b.b[b],
-// order arbitrary; the scans do not depend on it); active hubs go to the
-// small-hub list or, for large ones, their evaluate items to the item list.
-// Whole warps iterate together for the match.
+// order arbitrary; the scans do not depend on it); the hub bin's list holds
+// hub numbers (k_hub_route turns them into evaluate work once the round's
+// preparation has fixed every table's size). Whole warps iterate together
+// for the match.
 __global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __restrict__ bin_list, BinBounds bb,
-                                                int32_t* __restrict__ act, unsigned long long* __restrict__ cnt,
-                                                int32_t* __restrict__ ev, int32_t* __restrict__ small) {
+                                                int32_t* __restrict__ act, unsigned long long* __restrict__ cnt) {
   const int lane = threadIdx.x & 31;
   const int64_t total = bb.b[NBINS];
   const int64_t stride = (int64_t)gridDim.x * NT;
@@ -1585,23 +1639,37 @@ __global__ void __launch_bounds__(NT) k_compact(ScanCtx s, const int32_t* __rest
       bin = 0;
       while (i >= bb.b[bin + 1]) ++bin;
     }
-    if (bin == B_HUB) {
-      const int32_t h = (int32_t)(i - bb.b[B_HUB]);  // hub h is the h-th entry of the hub bin
-      if (s.hub_tab[h + 1] - s.hub_tab[h] <= HUB_SMALL) {
-        small[atomicAdd(&cnt[NBINS + 1], 1ull)] = h;
-      } else {
-        const int64_t e0 = s.hub_ev_first[h], ne = s.hub_ev_first[h + 1] - e0;
-        const unsigned long long p = atomicAdd(&cnt[NBINS], (unsigned long long)ne);
-        for (int64_t j = 0; j < ne; ++j) ev[p + j] = (int32_t)(e0 + j);
-      }
-    }
-    const int key = bin != B_HUB ? bin : -1;
+    const int key = bin;
     const unsigned peers = __match_any_sync(FULL, key);
     const int leader = __ffs(peers) - 1;
     unsigned long long p0 = 0;
     if (key >= 0 && lane == leader) p0 = atomicAdd(&cnt[key], (unsigned long long)__popc(peers));
     p0 = __shfl_sync(FULL, p0, leader);
-    if (key >= 0) act[bb.b[key] + (int64_t)p0 + __popc(peers & ((1u << lane) - 1u))] = v;
+    // hub h is the h-th entry of the hub bin
+    if (key >= 0)
+      act[bb.b[key] + (int64_t)p0 + __popc(peers & ((1u << lane) - 1u))] =
+          key == B_HUB ? (int32_t)(i - bb.b[B_HUB]) : v;
+  }
+}
+
+// The evaluate work of the hubs examined this round, by the size of their
+// tables after this round's preparation: a hub with at most HUB_SMALL slots in
+// use goes to the one-warp list, a larger one's first ceil(cc / HUB_SLICE)
+// items to the item list. cnt[0] and cnt[1] count them (zeroed before).
+__global__ void __launch_bounds__(NT) k_hub_route(ScanCtx s, int32_t* __restrict__ ev, int32_t* __restrict__ small,
+                                                  unsigned long long* __restrict__ cnt) {
+  const int64_t n = s.hub_act ? (int64_t)*s.hub_act_cnt : s.nhubs;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
+    const int32_t h = s.hub_act ? s.hub_act[i] : (int32_t)i;
+    const int64_t cc = s.hub_cc[h];
+    if (cc <= HUB_SMALL) {
+      small[atomicAdd(&cnt[1], 1ull)] = h;
+    } else {
+      const int64_t e0 = s.hub_ev_first[h], ne = (cc + HUB_SLICE - 1) / HUB_SLICE;
+      const unsigned long long p = atomicAdd(&cnt[0], (unsigned long long)ne);
+      for (int64_t j = 0; j < ne; ++j) ev[p + j] = (int32_t)(e0 + j);
+    }
   }
 }
 
@@ -1921,6 +1989,10 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     {
       KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
+      // the examined hubs' evaluate work, by the table sizes the preparation left
+      CD_CHECK(cudaMemsetAsync(g->act_cnt + NBINS, 0, 2 * sizeof(unsigned long long), st));
+      CD_LAUNCH(k_hub_route<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(s, g->act_ev, g->act_small,
+                                                                             g->act_cnt + NBINS));
       CD_LAUNCH((k_hub_build_cl<W, 0><<<152 * 6, 256, hub_cl_smem<0>(), st>>>(s)));  // 6 CTAs per SM (registers)
       CD_LAUNCH((k_hub_build_cl<W, 1><<<456, HUB_NT, hub_cl_smem<1>(), st>>>(s)));
       CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, hub_cl_smem<2>(), st>>>(s)));
@@ -1936,9 +2008,8 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     const cudaStream_t sh = bs.s[1];
     {
       KTimer t(g, K_HUB_EVAL, 0.0, sh);
-      if (g->n_small_hubs > 0)
-        CD_LAUNCH(k_hub_eval_small<LOUV, NK><<<wave_grid(k_hub_eval_small<LOUV, NK>, NT, 0, (g->n_small_hubs + NW - 1) / NW),
-                                           NT, 0, sh>>>(s));
+      CD_LAUNCH(k_hub_eval_small<LOUV, NK><<<wave_grid(k_hub_eval_small<LOUV, NK>, NT, 0, (g->nhubs + NW - 1) / NW),
+                                         NT, 0, sh>>>(s));
       CD_LAUNCH(k_hub_eval<LOUV, NK><<<grid_cap(g->hub_eval_items, 152 * 8), NT, 0, sh>>>(s));
     }
     if (g->ktiming) mark(B_HUB);
@@ -2027,6 +2098,8 @@ int dispatch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned
 // The parts of a round's context that do not change from round to round.
 ScanCtx static_ctx(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool per_graph_stop) {
   ScanCtx s;
+  s.hub_act = nullptr;
+  s.hub_act_cnt = nullptr;
   s.off = g->off;
   s.cols = g->cols;
   s.w = g->w;
@@ -2051,6 +2124,8 @@ ScanCtx static_ctx(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool 
   s.hub_pref = g->hub_pref;
   s.hub_bits = g->hub_bits;
   s.hub_tab = g->hub_tab;
+  s.hub_cc = g->hub_cc;
+  s.hub_live = g->hub_live;
   s.hub_slot = g->hub_slot;
   s.hub_wide = g->hub_wide;
   s.hub_item_hub = g->hub_item_hub;
@@ -2140,10 +2215,12 @@ int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool p
   const bool compact = o.use_frontier && g->bin_start[NBINS] > 0;
   const int32_t* lists = compact ? g->act_list : g->bin_list;
   const unsigned long long* counts = compact ? g->act_cnt : g->full_cnt;
-  s.ev_list = compact ? g->act_ev : g->hub_big_items;
-  s.ev_cnt = (compact ? g->act_cnt : g->full_cnt) + NBINS;
-  s.small_list = compact ? g->act_small : g->hub_small;
-  s.small_cnt = (compact ? g->act_cnt : g->full_cnt) + NBINS + 1;
+  s.ev_list = g->act_ev;
+  s.ev_cnt = g->act_cnt + NBINS;
+  s.small_list = g->act_small;
+  s.small_cnt = g->act_cnt + NBINS + 1;
+  s.hub_act = compact ? g->act_list + g->bin_start[B_HUB] : nullptr;
+  s.hub_act_cnt = compact ? g->act_cnt + B_HUB : nullptr;
   const bool v32 = g->max_degw < ((int64_t)1 << 32);
 
   cudaGraph_t graph = nullptr, body = nullptr;
@@ -2198,7 +2275,7 @@ int device_rounds(cd_graph* g, const RunOpts& o, bool louv, bool use_s32, bool p
       BinBounds bb;
       for (int b = 0; b <= NBINS; ++b) bb.b[b] = g->bin_start[b];
       CD_LAUNCH(k_compact<<<wave_grid(k_compact, NT, 0, (g->bin_start[NBINS] + NT - 1) / NT), NT, 0, cap>>>(
-          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev, g->act_small));
+          s, g->bin_list, bb, g->act_list, g->act_cnt));
     }
     std::vector<std::pair<size_t, int>> marks;
     int rc2;
@@ -2364,23 +2441,23 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
     // frontier), else the active ones, compacted
     const int32_t* lists = g->bin_list;
     const unsigned long long* counts = g->full_cnt;
-    s.ev_list = g->hub_big_items;
-    s.ev_cnt = g->full_cnt + NBINS;
-    s.small_list = g->hub_small;
-    s.small_cnt = g->full_cnt + NBINS + 1;
+    s.ev_list = g->act_ev;
+    s.ev_cnt = g->act_cnt + NBINS;
+    s.small_list = g->act_small;
+    s.small_cnt = g->act_cnt + NBINS + 1;
+    s.hub_act = nullptr;
+    s.hub_act_cnt = nullptr;
     if (o.use_frontier && r > 0 && g->bin_start[NBINS] > 0) {
       KTimer t(g, K_FRONTIER, (double)g->bin_start[NBINS] * (4 + 1 + 4));
       CD_CHECK(cudaMemsetAsync(g->act_cnt, 0, (NBINS + 2) * sizeof(unsigned long long), st));
       BinBounds bb;
       for (int b = 0; b <= NBINS; ++b) bb.b[b] = g->bin_start[b];
       CD_LAUNCH(k_compact<<<wave_grid(k_compact, NT, 0, (g->bin_start[NBINS] + NT - 1) / NT), NT, 0, st>>>(
-          s, g->bin_list, bb, g->act_list, g->act_cnt, g->act_ev, g->act_small));
+          s, g->bin_list, bb, g->act_list, g->act_cnt));
       lists = g->act_list;
       counts = g->act_cnt;
-      s.ev_list = g->act_ev;
-      s.ev_cnt = g->act_cnt + NBINS;
-      s.small_list = g->act_small;
-      s.small_cnt = g->act_cnt + NBINS + 1;
+      s.hub_act = g->act_list + g->bin_start[B_HUB];
+      s.hub_act_cnt = g->act_cnt + B_HUB;
     }
     std::vector<std::pair<size_t, int>> marks;
     const bool v32 = g->max_degw < ((int64_t)1 << 32);
