@@ -257,7 +257,9 @@ int cd_server_destroy(cd_server* s);
  * (degree <= 1024) or 512 threads (<= 4096) with a shared-memory table, and
  * vertices above t_hub keep persistent label histograms updated by their
  * neighbours' moves. 32 <= t_warp <= 256, t_warp <= t_hub <= 4096; defaults
- * 256 and 1024. */
+ * 256 and 1024, except that a Louvain coarse graph of at least 2^27 arcs takes
+ * t_hub = 512 (its levels run many rounds that move few vertices). Thresholds
+ * set here (or by cd_autotune) are kept by every coarse graph made from g. */
 int cd_graph_set_bins(cd_graph* g, int32_t t_warp, int32_t t_hub);
 
 /* Autotuner: time `rounds` rounds of LPA plus `rounds` rounds of local moving

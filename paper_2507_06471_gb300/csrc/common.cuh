@@ -23,6 +23,15 @@ constexpr int WARP_MAX = 256;    // a warp per vertex, table <= 512 slots
 constexpr int BLK1_MAX = 1024;   // 128 threads per vertex, table <= 2048 slots
 constexpr int BLK4_MAX = 4096;   // a whole 512-thread CTA per vertex, table <= 8192 slots
 constexpr int BLOCK_MAX = 1024;  // default hub threshold (largest degree rescanned every round)
+// A coarse graph (a Louvain level after the first) of at least COARSE_HUB_ARCS
+// arcs takes the lower hub threshold COARSE_T_HUB unless the thresholds were
+// set on the graph it came from: such levels run many rounds that move few
+// vertices, where a persistent histogram costs less than rescanning a row of
+// 513..1024 arcs (measured: R-MAT 24 and 26 coarse levels 4-6% faster; R-MAT 22
+// no change; a 1M-vertex LFR-style graph, whose coarse graphs are far smaller,
+// 50% slower with the lower threshold, hence the size condition).
+constexpr int64_t COARSE_HUB_ARCS = (int64_t)1 << 27;
+constexpr int COARSE_T_HUB = 512;
 // The runtime bin boundaries t_warp (warp vs 128-thread group) and t_hub
 // (group vs hub histogram) may be lowered below these capacities (autotuner).
 constexpr int HUB_CHUNK = 4096;  // arcs per hub build/mark item (a 512-thread CTA, 8192-slot table)
@@ -133,6 +142,7 @@ struct cd_graph {
   bool cols_distinct = false;      // no row repeats a column (strictly increasing input rows, or coarse rows)
   int t_warp = cd::WARP_MAX;       // degrees 33..t_warp: a warp per vertex
   int t_hub = cd::BLOCK_MAX;       // degrees t_warp+1..t_hub: 128 threads (512 above 1024); above: hub
+  bool bins_set = false;           // thresholds chosen by cd_graph_set_bins / cd_autotune (kept by coarse graphs)
 
   // run state (allocated on first use)
   int32_t* C = nullptr;

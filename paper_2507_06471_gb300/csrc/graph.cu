@@ -704,6 +704,7 @@ int ingest(cd_graph* g, int loops_twice, unsigned long long* stats_host) {
 
 int rebin(cd_graph* g, int t_warp, int t_hub) {
   if (t_warp < 32 || t_warp > WARP_MAX || t_hub < t_warp || t_hub > BLK4_MAX) return CD_EINVAL;
+  g->bins_set = true;
   if (t_warp == g->t_warp && t_hub == g->t_hub && g->bin_list) return CD_OK;
   CD_CHECK(cudaStreamSynchronize(g->stream));
   free_bins(g);
@@ -747,6 +748,9 @@ int graph_adopt(cudaStream_t s, int64_t n, int64_t nnz, int64_t* off, int32_t* c
   if (like) {
     g->t_warp = like->t_warp;
     g->t_hub = like->t_hub;
+    g->bins_set = like->bins_set;
+    if (!g->bins_set && nnz >= COARSE_HUB_ARCS && g->t_hub > COARSE_T_HUB && g->t_warp <= COARSE_T_HUB)
+      g->t_hub = COARSE_T_HUB;
   }
   g->stream = s;
   g->n = n;
