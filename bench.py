@@ -89,7 +89,12 @@ def parse():
                          "level 0 to convergence, aggregates, then local moving on the coarse graph with "
                          "max_iter 3 and 4, the second inside cudaProfilerStart/Stop, and prints the "
                          "algorithmic bytes of round 3 per kernel; 'first-rounds' runs LPA and local moving "
-                         "with max_iter 2 (round 1 builds every hub table)")
+                         "with max_iter 2 (round 1 builds every hub table) and prints the algorithmic "
+                         "bytes of the LPA run per kernel")
+    ap.add_argument("--ncu-summary", nargs="+", default=None, metavar="CSV",
+                    help="summarise an ncu --csv launch list per kernel group (no GPU needed); with a "
+                         "--case JSON as second argument, record the DRAM bytes of the captured launches "
+                         "over their algorithmic bytes in profiles/traffic.json")
     return ap.parse_args()
 
 
@@ -292,22 +297,127 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """dram bytes per launch of `kernel` from a committed ncu summary, or None
-    if the summary is missing or was taken on other kernel sources."""
+# what the library counts as one launch's algorithmic bytes, per profile group
+KERNEL_BYTES = {
+    "hub_build": "hub-table builds: (column 4 + label 4 + weight) per arc of a rebuilt hub + 8 per table slot "
+                 "written (the implementation's data structure, not a per-round figure of the method; the "
+                 "method's per-round bytes are under 'rounds')",
+    "hub_prepare": "8 per hub-table slot cleared, or read and written by a compaction, + 8 per hub (routing)",
+    "hub_eval": "per live histogram entry 24 (+ 8 Sigma_tot for Louvain) + 12 per examined hub",
+    "hub_mark": "5 per arc of a moved hub (column, flag) + 64 per logged hub-histogram update",
+    "scan_warp": "per examined vertex 13 (+ 24 Louvain) + per scanned arc (column 4 + label 4 + weight) "
+                 "+ 8 per candidate pair (Louvain)",
+    "scan_blk128": "per examined vertex 13 (+ 24 Louvain) + per scanned arc (column 4 + label 4 + weight) "
+                   "+ 8 per candidate pair (Louvain)",
+}
+
+
+def sources_digest() -> str:
+    """Digest of the kernel sources a committed ncu figure was taken on."""
+    h = hashlib.sha256()
+    for name in ("scan.cu", "graph.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2507_06471_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, alg_bytes_per_launch: float):
+    """DRAM bytes per launch of `kernel` (a kernel group of the library's
+    profile), scaled from a small-case ncu capture: its measured DRAM bytes
+    over its algorithmic bytes, times this run's algorithmic bytes per launch.
+    None if no capture of the current kernel sources covers the group."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
-        return None
+        return None, None
     with open(path) as f:
-        d = json.load(f)
-    e = d.get(workload, {}).get(kernel)
-    if not e:
-        return None
-    src = os.path.join(ROOT, "paper_2507_06471_gb300", "csrc", "scan.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if e.get("scan_cu_sha") != digest:
-        return None
-    return e.get("dram_bytes_per_launch")
+        e = json.load(f).get(kernel)
+    if not e or e.get("sources") != sources_digest() or not e.get("alg_bytes"):
+        return None, None
+    ratio = e["dram_bytes"] / e["alg_bytes"]
+    return ratio * alg_bytes_per_launch, {"dram_over_alg": ratio, "from": e["case"], "capture": e["capture"]}
+
+
+def kernel_group(name: str) -> str:
+    """The library's profile group of a kernel named as ncu prints it."""
+    import re
+    m = re.search(r"\b(k_[A-Za-z0-9_]+)", name)
+    if not m:
+        return "input generator and PyTorch"
+    base = m.group(1)
+    rest = name[m.end():]
+    targs = rest[1:rest.find(">")].split(",") if rest.startswith("<") else []
+    if base in ("k_hub_prepare", "k_hub_route"):
+        return "hub_prepare"
+    if base in ("k_hub_build_cl", "k_hub_build"):
+        return "hub_build"
+    if base in ("k_hub_eval_small", "k_hub_eval"):
+        return "hub_eval"
+    if base in ("k_hub_mark", "k_hub_apply_log"):
+        return "hub_mark"
+    if base == "k_scan_group" and len(targs) > 3:
+        return "scan_blk" + targs[3].strip()
+    if base == "k_scan_tile" and targs:
+        return "scan_tile" + targs[0].strip()
+    if base == "k_scan_warp":
+        return "scan_warp"
+    if base == "k_first_round":
+        return "first round (every bin)"
+    if base == "k_compact":
+        return "frontier"
+    if base in ("k_apply_state", "k_sigma32_moves"):
+        return "apply_moves"
+    if base.startswith("k_ag_") or base.startswith("k_rs_"):
+        return "aggregation and radix sort"
+    return "other library kernels"
+
+
+def ncu_summary(csv_path: str, case_json: str = None):
+    """Per kernel group of an ncu --csv log: launches, time, share, and DRAM
+    bytes when the log has them. With a --case JSON, records each captured
+    group's DRAM bytes over its algorithmic bytes in profiles/traffic.json."""
+    import csv
+    hdr, rows = None, {}
+    for r in csv.reader(open(csv_path)):
+        if r and r[0] == "ID":
+            hdr = r
+            continue
+        if not hdr or len(r) != len(hdr):
+            continue
+        d = dict(zip(hdr, r))
+        e = rows.setdefault(d["ID"], {"name": d["Kernel Name"]})
+        v = float(d["Metric Value"].replace(",", ""))
+        unit = d["Metric Unit"]
+        if d["Metric Name"] == "gpu__time_duration.sum":
+            e["ms"] = v / 1e6 if unit == "ns" else (v / 1e3 if unit in ("us", "usecond") else v)
+        elif d["Metric Name"].startswith("dram__bytes_"):
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1)
+            e["dram"] = e.get("dram", 0.0) + v * scale
+    groups = {}
+    for e in rows.values():
+        g = groups.setdefault(kernel_group(e["name"]), {"launches": 0, "ms": 0.0, "dram": 0.0})
+        g["launches"] += 1
+        g["ms"] += e.get("ms", 0.0)
+        g["dram"] += e.get("dram", 0.0)
+    lib_ms = sum(g["ms"] for k, g in groups.items() if k != "input generator and PyTorch")
+    print("| kernel group | launches | ms | share of library time | DRAM MB |")
+    print("|---|---|---|---|---|")
+    for k, g in sorted(groups.items(), key=lambda kv: -kv[1]["ms"]):
+        share = f"{100 * g['ms'] / lib_ms:.1f}%" if k != "input generator and PyTorch" and lib_ms else "—"
+        print(f"| {k} | {g['launches']} | {g['ms']:.1f} | {share} | {g['dram'] / 1e6:.1f} |")
+    if not case_json:
+        return
+    case = json.load(open(case_json))
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
+    for k, g in groups.items():
+        alg = case["alg_bytes"].get(k)
+        if not alg or not g["dram"]:
+            continue
+        out[k] = {"dram_bytes": g["dram"], "alg_bytes": alg, "launches": g["launches"],
+                  "case": f"R-MAT {case['scale']}, {case['captured']} ({case['case']})",
+                  "capture": os.path.basename(csv_path), "sources": sources_digest()}
+        print(f"{k}: DRAM {g['dram'] / 1e6:.1f} MB / algorithmic {alg / 1e6:.1f} MB = {g['dram'] / alg:.2f}")
+    with open(path, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
@@ -734,10 +844,16 @@ def run_case(args):
     torch.cuda.empty_cache()
     G = cd.Graph(g.off, g.cols, None)
     if args.case == "first-rounds":
-        G.lpa(max_iter=2)
+        G.lpa(max_iter=2, timing=1)
+        alg = {x["name"]: x["alg_bytes"] for x in G.profile() if x["launches"]}
         G.local_move(max_iter=2)
         torch.cuda.synchronize()
-        print(json.dumps({"case": args.case, "n": G.n, "arcs": G.nnz}))
+        out = {"case": args.case, "scale": args.scale or 23, "n": G.n, "arcs": G.nnz,
+               "captured": "LPA round 1", "alg_bytes": alg}
+        print(json.dumps(out))
+        if args.json_out:
+            with open(args.json_out, "w") as f:
+                json.dump(out, f)
         return
     lab, _, _ = G.local_move()
     C, _ = G.aggregate(lab)
@@ -752,13 +868,21 @@ def run_case(args):
             torch.cuda.profiler.stop()
         prof[r] = {x["name"]: x["alg_bytes"] for x in C.profile() if x["launches"]}
     t = C.trace()[3]
-    print(json.dumps({"case": args.case, "n": C.n, "arcs": C.nnz,
-                      "round3": {"active": t["active"], "arcs": t["arcs"], "moved": t["moved"]},
-                      "alg_bytes_round3": {k: prof[4][k] - prof[3].get(k, 0.0) for k in prof[4]}}))
+    out = {"case": args.case, "scale": args.scale or 23, "n": C.n, "arcs": C.nnz,
+           "captured": "coarse-graph round 3",
+           "round3": {"active": t["active"], "arcs": t["arcs"], "moved": t["moved"]},
+           "alg_bytes": {k: prof[4][k] - prof[3].get(k, 0.0) for k in prof[4]}}
+    print(json.dumps(out))
+    if args.json_out:
+        with open(args.json_out, "w") as f:
+            json.dump(out, f)
 
 
 def main():
     args = parse()
+    if args.ncu_summary:
+        ncu_summary(*args.ncu_summary)
+        return
     rank, world, local = dist_setup()
     if args.case:
         run_case(args)
@@ -875,8 +999,7 @@ def run_graph(args, rank, world, local):
     dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
     dname, d = dom
     achieved = (d["alg_bytes"] / d["launches"]) / (d["total_ms"] / d["launches"] / 1e3) / 1e9
-    wl_name = f"{args.workload}" + (f"_scale{scale}" if scale else "")
-    traffic = ncu_traffic(dname, wl_name)
+    traffic, traffic_src = ncu_traffic(dname, d["alg_bytes"] / d["launches"])
     total_prof_ms = sum(v["total_ms"] for v in prof.values())
     kernels = {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3),
                    "share": round(v["total_ms"] / total_prof_ms, 4) if total_prof_ms else 0,
@@ -924,8 +1047,8 @@ def run_graph(args, rank, world, local):
         "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": args.e2e_steps, "ms_per_step": 1e3 * e2e_s / max(1, args.e2e_steps)},
         "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "bytes": "library-counted algorithmic bytes of the kernel (per-kernel table of the design notes)",
+                     "frac": achieved / peak, "traffic": traffic, "traffic_scaled_from": traffic_src,
+                     "bytes": KERNEL_BYTES.get(dname, "library-counted algorithmic bytes of the kernel"),
                      "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "kernels": kernels,
         "kernels_how": "one step after the timed region with per-kernel CUDA events on each kernel's stream "

@@ -65,10 +65,11 @@ enum Ctr {
   C_DEFERRED,    // vertices whose move the coin deferred
   C_BIN0,        // then per bin: active, arcs, candidates
   C_HUB_BARCS = C_BIN0 + 3 * NBINS,  // arcs read by hub table builds this round
-  C_HUB_BSLOTS,                      // table slots they (and the clears and compactions) wrote
+  C_HUB_BSLOTS,                      // table slots they wrote
   C_MARCS,                           // arcs of the vertices that moved this round
   C_HUB_MARCS,                       // arcs of the hubs that moved this round
   C_HUB_LOG,                         // hub-histogram updates logged this round
+  C_HUB_PSLOTS,                      // table slots cleared, or read and written by compactions
   C_COUNT
 };
 
@@ -76,7 +77,7 @@ enum Ctr {
 enum Kern {
   K_UPLOAD = 0, K_SCAN_T4, K_SCAN_T8, K_SCAN_T16, K_SCAN_T32, K_SCAN_WARP, K_SCAN_BLK128,
   K_HUB_INSERT, K_HUB_EVAL, K_APPLY, K_RENUMBER, K_AGG_EMIT, K_SORT, K_AGG_REDUCE, K_MODULARITY,
-  K_HUB_MARK, K_FRONTIER, K_SCAN_BLK512, K_COUNT
+  K_HUB_MARK, K_FRONTIER, K_SCAN_BLK512, K_HUB_PREP, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 

@@ -19,7 +19,7 @@ namespace cd {
 const char* const kKernelNames[K_COUNT] = {
     "ingest",     "scan_tile4", "scan_tile8", "scan_tile16", "scan_tile32", "scan_warp",
     "scan_blk128", "hub_build", "hub_eval",   "apply_moves", "renumber",    "agg_emit",
-    "radix_sort", "agg_reduce", "modularity", "hub_mark", "frontier", "scan_blk512"};
+    "radix_sort", "agg_reduce", "modularity", "hub_mark", "frontier", "scan_blk512", "hub_prepare"};
 
 static thread_local int g_last_cuda = 0;
 static std::atomic<long long> g_launches{0};

@@ -997,7 +997,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
           s.hub_cc[h] = nc;
           s.hub_used[h] = (int32_t)nl;
           s.hub_rb[h] = 0;
-          atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)(2 * cc));  // read and written
+          atomicAdd(&s.ctr[C_HUB_PSLOTS], (unsigned long long)(2 * cc));  // read and written
         }
         __syncthreads();
         continue;
@@ -1017,7 +1017,7 @@ __global__ void __launch_bounds__(NT) k_hub_prepare(ScanCtx s) {
     {  // giant or two-word hubs: cleared here (the slots past cc are empty already),
        // built by items with global inserts
       const int64_t clr = s.hub_wide ? cap : cc;
-      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_BSLOTS], (unsigned long long)clr);
+      if (threadIdx.x == 0) atomicAdd(&s.ctr[C_HUB_PSLOTS], (unsigned long long)clr);
       for (int64_t i = threadIdx.x; i < clr; i += NT) {
         if (!s.hub_wide) {
           s.hub_slot[base + i] = SLOT_EMPTY;
@@ -1987,12 +1987,16 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
   auto mark = [&](int b) { marks.push_back({g->pending.size() - 1, b}); };
   if (cnt(B_HUB) > 0) {
     {
-      KTimer t(g, K_HUB_INSERT);  // clear + build run only when the rebuild flag is set
+      KTimer t(g, K_HUB_PREP);  // compactions, and clears of the tables rebuilt below
       CD_LAUNCH(k_hub_prepare<<<grid_cap(g->nhubs, 152 * 2), NT, HUB_PREP_SMEM, st>>>(s));
       // the examined hubs' evaluate work, by the table sizes the preparation left
       CD_CHECK(cudaMemsetAsync(g->act_cnt + NBINS, 0, 2 * sizeof(unsigned long long), st));
       CD_LAUNCH(k_hub_route<<<grid_cap((g->nhubs + NT - 1) / NT), NT, 0, st>>>(s, g->act_ev, g->act_small,
                                                                              g->act_cnt + NBINS));
+    }
+    if (g->ktiming) marks.push_back({g->pending.size() - 1, -2});
+    {
+      KTimer t(g, K_HUB_INSERT);  // the builds run only for hubs queued by the preparation
       CD_LAUNCH((k_hub_build_cl<W, 0><<<152 * 6, 256, hub_cl_smem<0>(), st>>>(s)));  // 6 CTAs per SM (registers)
       CD_LAUNCH((k_hub_build_cl<W, 1><<<456, HUB_NT, hub_cl_smem<1>(), st>>>(s)));
       CD_LAUNCH((k_hub_build_cl<W, 2><<<304, HUB_NT, hub_cl_smem<2>(), st>>>(s)));
@@ -2498,6 +2502,8 @@ int run_rounds(cd_graph* g, const RunOpts& o, bool louv, int64_t* moves_out, int
         bytes = (double)fa * (8 + 4 + 1) + (double)farcs * (4 + wbytes) + (louv ? (double)fa * 24 + (double)fc * 8 : 0.0);
       } else if (b == -1)  // hub table builds: the arcs they read, the slots they wrote
         bytes = (double)h[C_HUB_BARCS] * (4 + 4 + wbytes) + (double)h[C_HUB_BSLOTS] * 8;
+      else if (b == -2)  // hub preparation: slots cleared, or read and written by compactions; the route
+        bytes = (double)h[C_HUB_PSLOTS] * 8 + (double)g->nhubs * 8;
       else if (b == B_HUB)  // hub evaluate: the candidates of every active hub
         bytes = (double)cb * (12 + 12 + (louv ? 8 : 0)) + (double)ab * (8 + 4);
       else
