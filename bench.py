@@ -375,22 +375,36 @@ def ncu_summary(csv_path: str, case_json: str = None):
     bytes when the log has them. With a --case JSON, records each captured
     group's DRAM bytes over its algorithmic bytes in profiles/traffic.json."""
     import csv
-    hdr, rows = None, {}
+    to_ms = {"ns": 1e-6, "nsecond": 1e-6, "us": 1e-3, "usecond": 1e-3, "ms": 1.0, "msecond": 1.0}
+    to_b = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    hdr, units, rows = None, None, {}
     for r in csv.reader(open(csv_path)):
         if r and r[0] == "ID":
-            hdr = r
+            hdr, units = r, None
             continue
         if not hdr or len(r) != len(hdr):
             continue
         d = dict(zip(hdr, r))
+        if "Metric Name" in d:  # one row per metric (ncu --csv --log-file)
+            e = rows.setdefault(d["ID"], {"name": d["Kernel Name"]})
+            v = float(d["Metric Value"].replace(",", ""))
+            unit = d["Metric Unit"]
+            if d["Metric Name"] == "gpu__time_duration.sum":
+                e["ms"] = v * to_ms.get(unit, 1e-6)
+            elif d["Metric Name"] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+                e["dram"] = e.get("dram", 0.0) + v * to_b.get(unit, 1)
+            continue
+        if not d["ID"]:  # the units row of a raw page (ncu -i report --page raw --csv)
+            units = d
+            continue
         e = rows.setdefault(d["ID"], {"name": d["Kernel Name"]})
-        v = float(d["Metric Value"].replace(",", ""))
-        unit = d["Metric Unit"]
-        if d["Metric Name"] == "gpu__time_duration.sum":
-            e["ms"] = v / 1e6 if unit == "ns" else (v / 1e3 if unit in ("us", "usecond") else v)
-        elif d["Metric Name"].startswith("dram__bytes_"):
-            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}.get(unit, 1)
-            e["dram"] = e.get("dram", 0.0) + v * scale
+        u = units or {}
+        if d.get("gpu__time_duration.sum"):
+            e["ms"] = float(d["gpu__time_duration.sum"].replace(",", "")) * to_ms.get(
+                u.get("gpu__time_duration.sum", "nsecond"), 1e-6)
+        for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            if d.get(k):
+                e["dram"] = e.get("dram", 0.0) + float(d[k].replace(",", "")) * to_b.get(u.get(k, "byte"), 1)
     groups = {}
     for e in rows.values():
         g = groups.setdefault(kernel_group(e["name"]), {"launches": 0, "ms": 0.0, "dram": 0.0})

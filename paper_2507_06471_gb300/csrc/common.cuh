@@ -199,7 +199,7 @@ int dev_alloc_t(T** p, int64_t count, cudaStream_t s) {
   return dev_alloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(T), s);
 }
 
-// profiling helpers: bracket a launch with events when timing is on
+// profiling helpers: bracket a launch with events when per-kernel timing is on
 struct KTimer {
   cd_graph* g;
   int k;
