@@ -367,6 +367,33 @@ def test_bins_do_not_change_results(bins):
     assert levels == olv and np.array_equal(lab.cpu().numpy(), olab)
 
 
+def test_hub_tables_shrink_and_keep_results():
+    # a low hub threshold makes hubs of many vertices whose neighbourhoods end in
+    # few communities, so their tables are compacted below their allocation
+    # (the preparation then reads and writes slots); every trace field still
+    # equals the oracle's
+    g = graph("rmat16")
+    off, cols, w = g.numpy()
+    nh = int((np.diff(off) > 64).sum())
+    G = upload(g)
+    cd.cd_graph_set_bins(G.h, 32, 64)
+    compacted = 0.0
+    lab, rounds = G.lpa(timing=1)
+    olab, otr = oracle.lpa(off, cols, w)
+    assert rounds == otr.rounds and np.array_equal(lab.cpu().numpy(), olab)
+    same_trace(G.trace(), otr)
+    p = {x["name"]: x for x in G.profile()}["hub_prepare"]
+    compacted += p["alg_bytes"] - 8.0 * nh * p["launches"]
+    lab, moves, rounds = G.local_move(timing=1)
+    olab, omoves, otr = oracle.local_move(off, cols, w)
+    assert (moves, rounds) == (omoves, otr.rounds)
+    np.testing.assert_array_equal(lab.cpu().numpy(), olab)
+    same_trace(G.trace(), otr)
+    p = {x["name"]: x for x in G.profile()}["hub_prepare"]
+    compacted += p["alg_bytes"] - 8.0 * nh * p["launches"]
+    assert compacted > 0  # slots were compacted (no hub here is large enough for a cleared global build)
+
+
 def test_autotune_keeps_results():
     g = graph("rmat16")
     off, cols, w = g.numpy()
