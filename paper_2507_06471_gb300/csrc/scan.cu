@@ -1882,6 +1882,8 @@ double scan_bytes(bool louv, int wbytes, int64_t act, int64_t arcs, int64_t cand
   return b;
 }
 
+constexpr int64_t CONC_LOUV_BYTES = (int64_t)64 << 20;  // half of the 129 MB L2, rounded down
+
 // Scan kernels of different bins may run concurrently when none of them
 // writes what another reads: hub histograms are then only read during the
 // scans (their updates go to the log, applied after the join). fork() makes
@@ -2006,8 +2008,14 @@ int launch_round(cd_graph* g, ScanCtx& s, const int32_t* lists, const unsigned l
     }
     if (g->ktiming) marks.push_back({g->pending.size() - 1, -1});
   }
-  // the scans of the bins, concurrently when the hub histograms are only read
-  const BinStreams bs = fork_bins(g, !s.async_mode && (g->nhubs == 0 || s.hub_log != nullptr));
+  // the scans of the bins, concurrently when the hub histograms are only read,
+  // except for Louvain on a graph whose labels and Sigma_tot copy (8 bytes per
+  // vertex) exceed half of L2: there the concurrent bins' random gathers
+  // evict one another (measured at R-MAT 26: Louvain 2.62 s concurrent, 2.51 s
+  // one bin after another; LPA 353 vs 366 ms and R-MAT 22 Louvain 164 vs
+  // 183 ms in favour of running them concurrently)
+  const bool conc = !LOUV || g->n * 8 <= CONC_LOUV_BYTES;
+  const BinStreams bs = fork_bins(g, conc && !s.async_mode && (g->nhubs == 0 || s.hub_log != nullptr));
   if (cnt(B_HUB) > 0) {
     const cudaStream_t sh = bs.s[1];
     {
