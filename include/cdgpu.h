@@ -97,7 +97,13 @@ typedef struct cd_round_trace {
   int64_t moved_arcs; /* arcs of the vertices that moved (their neighbours are flagged) */
 } cd_round_trace;
 
-/* Per-kernel totals of the last run (cd_profile_get; timing = 1). */
+/* Per-kernel totals of the last run (cd_profile_get; timing = 1). One entry per
+ * launch group: ingest, scan_tile4/8/16/32, scan_warp, scan_blk128, scan_blk512
+ * (the degree bins' scans; round 0 of a run is counted under its bin),
+ * hub_prepare (hub-table compactions, clears and routing), hub_build (hub-table
+ * builds), hub_eval, hub_mark (flags and logged hub-histogram updates of
+ * committed moves), apply_moves, frontier, renumber, agg_emit, radix_sort,
+ * agg_reduce, modularity. */
 typedef struct cd_kernel_profile {
   char name[32];
   int64_t launches;
